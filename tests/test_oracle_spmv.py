@@ -1,0 +1,214 @@
+"""Pins of the SpMV oracle (Section 4, Listing 2, Remark 3): hand-worked
+values, exact arithmetic, the dense product, the componentwise error bound,
+and sensitivity to planted mistakes."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import c_listing2 as C
+from oracle import dacsr as D
+from oracle import spmv as S
+
+
+def _random_csr(rng, nr, nc, density=0.2, empty_rows=True):
+    mask = rng.random((nr, nc)) < density
+    if empty_rows:
+        mask[rng.integers(0, nr, size=max(1, nr // 10))] = False
+    rows, cols = np.nonzero(mask)
+    vals = rng.standard_normal(len(rows))
+    return W.from_coo(nr, rows, cols, vals)
+
+
+def _dense(nr, nc, rp, c, v):
+    A = np.zeros((nr, nc))
+    for r in range(nr):
+        for i in range(rp[r], rp[r + 1]):
+            A[r, c[i]] += v[i]
+    return A
+
+
+def test_example1_by_hand():
+    rp, c, v = W.example1_pattern()             # values 1..5
+    x = np.array([1.0, 2.0, 3.0, 4.0])
+    off = D.translate(4, rp, c)
+    expect = [1.0 * 1, 2.0 * 3, 3.0 * 2 + 4.0 * 4, 5.0 * 4]
+    assert S.spmv(4, rp, c, v, x, diagonal_addressed=False).tolist() == expect
+    assert S.spmv(4, rp, off, v, x).tolist() == expect
+    assert S.spmv_rows(4, rp, off, v, x).tolist() == expect
+    # alpha, beta: y <- 2 A x - 1 y
+    y = np.array([1.0, 1.0, 1.0, 1.0])
+    assert S.spmv(4, rp, off, v, x, y, 2.0, -1.0).tolist() == [2 * e - 1 for e in expect]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_row_loop_equals_vectorised(seed):
+    rng = np.random.default_rng(seed)
+    nr, nc = int(rng.integers(1, 60)), int(rng.integers(1, 60))
+    rp, c, v = _random_csr(rng, nr, nc)
+    off = D.translate(nr, rp, c)
+    x = rng.standard_normal(nc)
+    y = rng.standard_normal(nr)
+    for a, b in [(1.0, 0.0), (-1.5, 0.25)]:
+        for dt in (np.float64, np.float32):
+            r1 = S.spmv_rows(nr, rp, off, v, x, y, a, b, dtype=dt)
+            r2 = S.spmv(nr, rp, off, v, x, y, a, b, dtype=dt)
+            r3 = S.spmv(nr, rp, c, v, x, y, a, b, diagonal_addressed=False, dtype=dt)
+            assert np.array_equal(r1, r2) and np.array_equal(r2, r3)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_dense_and_exact_within_bound(seed):
+    rng = np.random.default_rng(10 + seed)
+    nr, nc = int(rng.integers(1, 50)), int(rng.integers(1, 50))
+    rp, c, v = _random_csr(rng, nr, nc, density=0.3)
+    off = D.translate(nr, rp, c)
+    x = rng.standard_normal(nc)
+    y = rng.standard_normal(nr)
+    A = _dense(nr, nc, rp, c, v)
+    for a, b in [(1.0, 0.0), (0.75, -2.0)]:
+        got = S.spmv(nr, rp, off, v, x, y, a, b)
+        ex = S.spmv_exact(nr, rp, off, v, x, y, a, b)
+        bnd = S.error_bound(nr, rp, off, v, x, y, a, b)
+        assert np.all(np.abs(got - ex) <= bnd)
+        dense = a * (A @ x) + (b * y if b != 0 else 0.0)
+        assert np.all(np.abs(dense - ex) <= 2 * bnd)
+
+
+def test_dyadic_is_exact():
+    rp, c, v = W.laplace2d_5pt(64)
+    n = 64 * 64
+    x = W.dyadic_vector(n, W.rng_for(1, 1))
+    off = D.translate(n, rp, c)
+    got = S.spmv(n, rp, off, v, x)
+    assert np.array_equal(got, S.spmv_exact(n, rp, off, v, x))
+    # also exact in FP32: every partial sum is a multiple of 2^-20 below 2^3
+    got32 = S.spmv_lowp(n, rp, off, v, x.astype(np.float32))
+    assert np.array_equal(got32.astype(np.float64), got)
+
+
+def test_beta_zero_ignores_y_and_empty_rows():
+    rp = np.array([0, 2, 2, 3], dtype=np.int32)
+    c = np.array([0, 2, 1], dtype=np.int32)
+    v = np.array([1.0, 2.0, 3.0])
+    x = np.array([1.0, 1.0, 1.0])
+    y = np.array([np.nan, np.inf, np.nan])
+    out = S.spmv(3, rp, c, v, x, y, 1.0, 0.0, diagonal_addressed=False)
+    assert out.tolist() == [3.0, 0.0, 3.0]
+    out = S.spmv(3, rp, c, v, x, np.array([1.0, 5.0, 1.0]), 1.0, 2.0, diagonal_addressed=False)
+    assert out.tolist() == [5.0, 10.0, 5.0]
+
+
+def test_tall_matrix_remark3():
+    # nrows > ncols: x shifted by the row points outside x but is only read
+    # at in-range columns
+    rp, c, v = W.from_coo(6, [0, 3, 5, 5], [0, 1, 0, 2], [1.0, 2.0, 3.0, 4.0])
+    off = D.translate(6, rp, c)
+    x = np.array([10.0, 20.0, 30.0])
+    assert S.spmv(6, rp, off, v, x).tolist() == [10.0, 0.0, 0.0, 40.0, 0.0, 150.0]
+
+
+@pytest.mark.parametrize("nthreads", [1, 3])
+def test_c_listing2_bitwise(nthreads):
+    rng = np.random.default_rng(7)
+    n = 3000
+    rp, c, v = W.random_banded(n, 100, rng)
+    off = D.translate(n, rp, c).astype(np.int16)
+    x = rng.uniform(-1, 1, n)
+    y = rng.standard_normal(n)
+    for a, b in [(1.0, 0.0), (-0.5, 1.25)]:
+        ref = S.spmv(n, rp, off, v, x, y, a, b)
+        assert np.array_equal(C.spmv_dacsr16(n, rp, off, v, x, y, a, b, nthreads), ref)
+        assert np.array_equal(C.spmv_csr32(n, rp, c, v, x, y, a, b, nthreads), ref)
+
+
+def test_round_to_bf16_by_hand():
+    one = 1.0
+    cases = [
+        (1.0, 1.0),
+        (1 + 2 ** -8, 1.0),                    # halfway, tie to even (down)
+        (1 + 3 * 2 ** -8, 1 + 2 ** -6),        # halfway, tie to even (up)
+        (1 + 2 ** -8 + 2 ** -40, 1 + 2 ** -7),  # just above halfway: one rounding, not two
+        (-(1 + 2 ** -7), -(1 + 2 ** -7)),
+        (26.5, 26.5),
+        (0.1, 0.10009765625),
+        (2.0 ** -133, 2.0 ** -133),             # smallest bf16 subnormal
+        (2.0 ** -135, 0.0),
+        (3.4e38, np.inf),
+    ]
+    got = S.round_to_bf16([a for a, _ in cases])
+    assert got.tolist() == [b for _, b in cases]
+
+
+def test_round_to_bf16_matches_torch_on_fp32_inputs():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    v = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-30, 30, 20000),
+                        rng.standard_normal(1000) * 1e-39]).astype(np.float32)
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(S.round_to_bf16(v.astype(np.float64)), ref)
+
+
+def test_lowp_spmv_bound():
+    rng = np.random.default_rng(5)
+    n = 500
+    rp, c, v = W.random_banded(n, 30, rng)
+    off = D.translate(n, rp, c)
+    x32 = rng.uniform(-1, 1, n).astype(np.float32)
+    for q in ("f32", "bf16"):
+        vq = S.quantize(v, q)
+        got = S.spmv_lowp(n, rp, off, vq, x32)
+        ex = S.spmv_exact(n, rp, off, vq, x32.astype(np.float64))
+        bnd = S.error_bound(n, rp, off, vq, x32, u=S.U32)
+        assert np.all(np.abs(got - ex) <= bnd)
+        # quantisation error of the values against the FP64 matrix
+        ex64 = S.spmv_exact(n, rp, off, v, x32.astype(np.float64))
+        u_v = S.U32 if q == "f32" else S.UBF16
+        tot = bnd + u_v * S.abs_row_sums(n, rp, off, v, x32)
+        assert np.all(np.abs(got - ex64) <= tot)
+
+
+def test_spmm_columns():
+    rng = np.random.default_rng(9)
+    n = 200
+    rp, c, v = W.random_banded(n, 20, rng)
+    off = D.translate(n, rp, c)
+    X = rng.uniform(-1, 1, (n, 4))
+    Y = S.spmm(n, rp, off, v, X)
+    A = _dense(n, n, rp, c, v)
+    for j in range(4):
+        assert np.array_equal(Y[:, j], S.spmv(n, rp, off, v, X[:, j]))
+    bnd = np.stack([S.error_bound(n, rp, off, v, X[:, j]) for j in range(4)], 1)
+    assert np.all(np.abs(Y - A @ X) <= 2 * bnd)
+
+
+@pytest.mark.parametrize("mistake", ["index_sign", "dropped_term", "transposed", "value_sign",
+                                     "beta_ignored"])
+def test_planted_mistakes_are_caught(mistake, monkeypatch):
+    """Each plausible slip in the oracle breaks the dense-product check."""
+    rng = np.random.default_rng(11)
+    nr = nc = 40
+    rp, c, v = _random_csr(rng, nr, nc, density=0.25, empty_rows=False)
+    off = D.translate(nr, rp, c)
+    x = rng.standard_normal(nc)
+    y = rng.standard_normal(nr)
+    A = _dense(nr, nc, rp, c, v)
+    a, b = 1.5, 0.5
+    if mistake == "index_sign":
+        monkeypatch.setattr(S, "_columns",
+                            lambda n, p, i, da: (D.entry_rows(n, p) - np.asarray(i, dtype=np.int64)) % nc)
+        got = S.spmv(nr, rp, off, v, x, y, a, b)
+    elif mistake == "dropped_term":
+        rp_short = rp.copy()
+        got = np.zeros(nr)
+        for r in range(nr):
+            got[r] = a * sum(v[i] * x[c[i]] for i in range(rp_short[r], rp_short[r + 1] - 1)) + b * y[r]
+    elif mistake == "transposed":
+        rpT, cT, vT = W.from_coo(nc, c, D.entry_rows(nr, rp), v)
+        got = S.spmv(nc, rpT, cT, vT, x, y, a, b, diagonal_addressed=False)
+    elif mistake == "value_sign":
+        got = S.spmv(nr, rp, off, -v, x, y, a, b)
+    else:
+        got = S.spmv(nr, rp, off, v, x, y, a, 0.0)
+    dense = a * (A @ x) + b * y
+    bnd = S.error_bound(nr, rp, off, v, x, y, a, b)
+    assert np.any(np.abs(got - dense) > 2 * bnd)
