@@ -1,0 +1,316 @@
+/*
+ * damn.h -- C ABI of the GB300 (sm_103a) DA-CSR sparse matrix library.
+ *
+ * Diagonally-addressed CSR (DA-CSR) stores, for every stored entry of row r
+ * with column c, the offset c - r instead of c (Saak & Schulze,
+ * "Diagonally-Addressed Matrix Nicknack", arXiv 2307.06305, Section 2).  When
+ * every offset fits a signed 16-bit integer the index stream shrinks from 4 to
+ * 2 bytes per entry, and a memory-bound SpMV streams fewer bytes (Eq. (1),
+ * Eq. (3), Fig. 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers are DEVICE pointers unless their name starts with h_ (host).
+ *   The caller owns every buffer; the library never frees caller memory.
+ * - Scratch memory comes from a caller-provided device workspace whose size
+ *   is given by the matching *_workspace_size() query (16-byte aligned).
+ *   Only plan handles (*_plan_create) allocate device memory of their own.
+ * - stream is a cudaStream_t passed as void*; NULL means the legacy default
+ *   stream.  Calls are asynchronous on stream unless documented as
+ *   synchronising.
+ * - Every function returns a status code (DAMN_OK = 0 or a negative
+ *   DAMN_ERR_*); damn_last_error() returns a message for the calling thread.
+ *   No exception crosses the ABI and nothing aborts the process.
+ * - Matrices use CSR arrays: rowptr int32[nrows+1] (rowptr[0] = 0,
+ *   rowptr[nrows] = nnz, non-decreasing) and per entry a column index
+ *   col int32[nnz] (CSR-32) or a diagonal offset off int16[nnz] (DA-CSR-16),
+ *   plus values val[nnz].  Argument checks are O(1) host checks (sizes,
+ *   null pointers, alignment, dtype); damn_validate_csr() checks the arrays.
+ * - dtype selects the value type: DAMN_F64 (values, x and y FP64, FP64
+ *   accumulation), DAMN_F32 or DAMN_BF16 (values FP32 / BF16; x and y FP32;
+ *   FP32 accumulation).  val, x, y, col and off must be 16-byte aligned
+ *   (torch allocations are); misaligned pointers are rejected with
+ *   DAMN_ERR_INVALID_ARG.
+ */
+#ifndef DAMN_H
+#define DAMN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Status codes, types, diagnostics                                          */
+/* ------------------------------------------------------------------------ */
+#define DAMN_OK                  0
+#define DAMN_ERR_INVALID_ARG    -1 /* bad size, pointer, alignment or dtype      */
+#define DAMN_ERR_NOFIT          -2 /* an offset c - r lies outside int16 range  */
+#define DAMN_ERR_CUDA           -3 /* a CUDA runtime call failed                  */
+#define DAMN_ERR_NOT_CONVERGED  -4 /* an iterative solver hit its iteration cap  */
+#define DAMN_ERR_TIMEOUT        -5 /* a bounded device-side wait gave up          */
+#define DAMN_ERR_UNSUPPORTED    -6 /* valid request the library does not handle   */
+
+#define DAMN_F64   0
+#define DAMN_F32   1
+#define DAMN_BF16  2
+
+#define DAMN_FMT_CSR32   0
+#define DAMN_FMT_DACSR16 1
+
+/* Message describing the last error reported to the calling host thread. */
+const char *damn_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int damn_version(void);
+
+/* Reads the library's device status word for the current device (DAMN_OK
+ * or DAMN_ERR_TIMEOUT after a bounded wait inside a kernel gave up) into
+ * *h_status and clears it when reset != 0.  Synchronises stream. */
+int damn_device_status(int32_t *h_status, int reset, void *stream);
+
+/* Failure-detection self test: launches one kernel that waits on a device
+ * barrier which nothing ever completes, with a wait limit of timeout_ns
+ * nanoseconds (1e3 .. 1e10).  The kernel records DAMN_ERR_TIMEOUT in the
+ * device status word and returns; the call synchronises and returns
+ * DAMN_ERR_TIMEOUT when the bounded wait worked as designed (the device status
+ * word is cleared afterwards).  No fault, trap or hang is involved. */
+int damn_selftest_wait_timeout(int64_t timeout_ns, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* a1: CSR -> DA-CSR-16 translation and fit check (Section 2, Example 1,     */
+/*     Eq. (2); fit reading: every c - r in [-32768, 32767])                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t min_off;  /* smallest c - r over stored entries (0 if nnz == 0)      */
+  int32_t max_off;  /* largest c - r (0 if nnz == 0)                            */
+  int64_t w;        /* Eq. (2) bandwidth max |c - r|                           */
+  int64_t n_fit;    /* entries with c - r in [-32768, 32767]                    */
+  int64_t n_bad;    /* entries whose column lies outside [0, ncols)             */
+  int32_t fits;     /* 1 iff n_fit == nnz and n_bad == 0                         */
+  int32_t reserved;
+} damn_fit_info;
+
+/* Workspace bytes needed by damn_csr_to_dacsr. */
+size_t damn_csr_to_dacsr_workspace_size(void);
+
+/* off_out[i] = col[i] - r_i (narrowed to int16) for every stored entry i of
+ * row r_i; entry order and values are unchanged (values are not touched).
+ * Also computes the fit information into *h_info (always filled).
+ * Synchronises stream.  Returns DAMN_ERR_NOFIT when some offset does not fit
+ * int16 or a column is out of range; off_out is then unspecified.
+ * rowptr and col are device arrays; nrows, ncols >= 0; nnz < 2^31. */
+int damn_csr_to_dacsr(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                      const int32_t *col, int16_t *off_out, damn_fit_info *h_info,
+                      void *workspace, size_t ws_bytes, void *stream);
+
+/* Workspace bytes needed by damn_validate_csr. */
+size_t damn_validate_csr_workspace_size(void);
+
+/* Checks rowptr[0] == 0, rowptr[nrows] == nnz, rowptr non-decreasing and
+ * every col in [0, ncols).  *h_bad_rows receives the number of r with
+ * rowptr[r] > rowptr[r+1] (plus 1 when an end point is wrong), *h_bad_cols
+ * the number of out-of-range columns.  Synchronises stream.  Returns
+ * DAMN_ERR_INVALID_ARG when either count is non-zero. */
+int damn_validate_csr(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                      const int32_t *col, int64_t *h_bad_rows, int64_t *h_bad_cols,
+                      void *workspace, size_t ws_bytes, void *stream);
+
+/* Round-to-nearest-even conversion of n values: FP64 -> FP32 or BF16 (one
+ * rounding step, no double rounding through FP32), or FP32 -> BF16.  Used to
+ * make the reduced-precision copy of a matrix's values. */
+int damn_cast_values(int64_t n, const void *src, int src_dtype, void *dst, int dst_dtype,
+                     void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* a2: reverse Cuthill-McKee ordering and symmetric permutation             */
+/*     (Section 2, Example 2; Section 3)                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Host-side RCM ordering of a square pattern (host arrays).  Graph: pattern of
+ * A + A^T without self loops; components by smallest vertex; George-Liu
+ * pseudo-peripheral start from the component's minimum-degree vertex;
+ * neighbours appended by (degree, index); the concatenation reversed.
+ * h_perm[new] = old.  Optionally returns the bandwidth before / after.
+ * Runs on the calling host thread; no device work. */
+int damn_rcm_order(int32_t n, int64_t nnz, const int32_t *h_rowptr, const int32_t *h_col,
+                   int32_t *h_perm, int64_t *h_w_before, int64_t *h_w_after);
+
+/* Workspace bytes needed by damn_permute_sym for an n x n matrix. */
+size_t damn_permute_sym_workspace_size(int32_t n);
+
+/* B = P A P^T on the device: row i of B is row perm[i] of A, every column c
+ * becomes iperm[c], and each row is sorted by new column (entries with equal
+ * columns keep their stored order).  val/val_out have type dtype (F64, F32,
+ * BF16; may be NULL to permute the pattern only).  Asynchronous. */
+int damn_permute_sym(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
+                     const void *val, int dtype, const int32_t *perm, int32_t *rowptr_out,
+                     int32_t *col_out, void *val_out, void *workspace, size_t ws_bytes,
+                     void *stream);
+
+typedef struct {
+  int64_t w_before;  /* Eq. (2) bandwidth of A          */
+  int64_t w_after;   /* Eq. (2) bandwidth of P A P^T    */
+} damn_bw_info;
+
+/* Convenience: copies the pattern to the host, runs damn_rcm_order, copies
+ * perm to perm_out (device) and runs damn_permute_sym.  Synchronises. */
+int damn_rcm_permute(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
+                     const void *val, int dtype, int32_t *perm_out, int32_t *rowptr_out,
+                     int32_t *col_out, void *val_out, damn_bw_info *h_info, void *workspace,
+                     size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* a3/a4/a5/a8: SpMV y <- alpha A x + beta y (Section 4, Listing 2)           */
+/* ------------------------------------------------------------------------ */
+typedef struct damn_plan damn_plan;
+
+typedef struct {
+  int32_t mode;          /* 0 = one row per thread, 1 = balanced entry slices */
+  int32_t tile_items;    /* rows per tile, or rows+entries budget of a balanced tile */
+  int32_t ntiles;
+  int32_t grid;          /* persistent CTAs of the last launch                 */
+  int32_t stages;        /* shared-memory ring depth of the last launch        */
+  int32_t threads;       /* consumer threads per CTA                           */
+  double row_efficiency; /* nnz / (32 * sum over 32-row groups of max row len) */
+  int32_t max_row;       /* longest row                                        */
+  int32_t dtype;
+  int32_t tiling;        /* DAMN_TILING_*                                      */
+  int32_t x_staged_tiles;/* tiles whose x window is staged in shared memory    */
+} damn_plan_desc;
+
+/* Tilings (see damn_plan_set_tiling). */
+#define DAMN_TILING_SLICES    0
+#define DAMN_TILING_ROWS      1
+#define DAMN_TILING_ROWS_LONG 2
+
+/* Builds a plan for one matrix and value dtype: the partition of the rows
+ * into tiles, the compute mode (chosen from the row-length statistics:
+ * DAMN_TILING_ROWS or _ROWS_LONG when rows are uniform inside 32-row groups,
+ * DAMN_TILING_SLICES otherwise) and, when idx (col for DAMN_FMT_CSR32, off
+ * for DAMN_FMT_DACSR16) is given, the x window of every tile: the tile's
+ * sorted distinct columns cut into at most 8 contiguous segments (gaps of up
+ * to 32 columns merged), staged in shared memory by the SpMV kernels so that
+ * x is not gathered from global memory (the band-window staging of DA-CSR).
+ * Tiles whose window does not fit gather x from global memory.  idx may be
+ * NULL (no x windows).  Reads rowptr/idx on the device; synchronises.
+ * rowptr and idx must stay valid while the plan is used.  The plan owns device
+ * memory until damn_plan_destroy.  One plan serves the CSR-32 and DA-CSR-16
+ * copies of the same matrix, giving bitwise equal results. */
+int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                     int format, const void *idx, int dtype, void *stream, damn_plan **out);
+
+/* Times the three tilings on the given operands (format DAMN_FMT_*; idx is
+ * col or off) and keeps the fastest in the plan.  y is overwritten.
+ * Synchronises stream. */
+int damn_plan_autotune(damn_plan *plan, int format, const void *idx, const void *val,
+                       const void *x, void *y, void *stream);
+
+/* Pins the plan's tiling: DAMN_TILING_SLICES (tiles balanced on rows +
+ * entries, each computed as balanced entry slices), DAMN_TILING_ROWS (224-row
+ * tiles, one row per thread; short rows), DAMN_TILING_ROWS_LONG (128-row
+ * tiles with larger stages, one row per thread; rows of a few dozen).
+ * Recomputes the x windows; synchronises the legacy default stream. */
+int damn_plan_set_tiling(damn_plan *plan, int tiling);
+
+int damn_plan_describe(const damn_plan *plan, damn_plan_desc *h_desc);
+int damn_plan_destroy(damn_plan *plan);
+
+/* y <- alpha A x + beta y with A in CSR-32 (col = absolute column indices).
+ * x has ncols entries, y nrows.  beta == 0: y is output only (never read).
+ * plan may be NULL (fixed row tiles, balanced slices).  For a given plan the
+ * result is bitwise identical to damn_spmv_dacsr16 on the same matrix. */
+int damn_spmv_csr32(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                    const int32_t *col, const void *val, int dtype, const void *x, void *y,
+                    double alpha, double beta, const damn_plan *plan, void *stream);
+
+/* Same with A in DA-CSR-16: entry i of row r multiplies x[r + off[i]]
+ * (Listing 2's shifted view of x; Remark 3 for nrows != ncols). */
+int damn_spmv_dacsr16(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                      const int16_t *off, const void *val, int dtype, const void *x, void *y,
+                      double alpha, double beta, const damn_plan *plan, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* a6: CG (FP64) and mixed-precision CG with iterative refinement            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t iterations;   /* CG steps (inner steps summed for CG-IR)           */
+  int32_t outer;        /* refinement steps (CG-IR), 0 for CG                */
+  int32_t converged;
+  int32_t reserved;
+  double relres;        /* last ||r|| / ||b|| (recurrence for CG, true for IR) */
+  double true_relres;   /* ||b - A x|| / ||b|| recomputed in FP64 at exit     */
+} damn_cg_result;
+
+size_t damn_cg_workspace_size(int32_t n);
+
+/* FP64 conjugate gradients on an SPD matrix in DA-CSR-16 with FP64 values:
+ * x (in: x0, out: solution), stop when ||r|| <= rtol ||b|| or after
+ * max_iter steps.  Synchronises; returns DAMN_ERR_NOT_CONVERGED at the cap. */
+int damn_cg(int32_t n, int64_t nnz, const int32_t *rowptr, const int16_t *off,
+            const double *val, const double *b, double *x, double rtol, int32_t max_iter,
+            const damn_plan *plan, damn_cg_result *h_res, void *workspace, size_t ws_bytes,
+            void *stream);
+
+size_t damn_cg_ir_workspace_size(int32_t n);
+
+/* Mixed-precision refinement: outer residual r = b - A x with the FP64
+ * values (FP64 accumulation), inner CG on A_low d = r/||r|| with val_low of
+ * type low_dtype (DAMN_F32 or DAMN_BF16), FP32 vectors, FP32 accumulation and
+ * FP64 dot products, to inner_rtol or max_inner steps; x += ||r|| d in FP64.
+ * plan64 / plan_low may be NULL.  Synchronises. */
+int damn_cg_ir(int32_t n, int64_t nnz, const int32_t *rowptr, const int16_t *off,
+               const double *val, const void *val_low, int low_dtype, const double *b,
+               double *x, double rtol, double inner_rtol, int32_t max_inner, int32_t max_outer,
+               const damn_plan *plan64, const damn_plan *plan_low, damn_cg_result *h_res,
+               void *workspace, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* a7: multi-RHS SpMM and the batched persistent launch                      */
+/* ------------------------------------------------------------------------ */
+
+/* Y = A X for one DA-CSR-16 matrix, X row-major ncols x k, Y row-major
+ * nrows x k (1 <= k <= 64).  dtype F64 (X, Y FP64) or F32 (X, Y FP32). */
+int damn_spmm_dacsr16(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                      const int16_t *off, const void *val, int dtype, int32_t k, const void *X,
+                      void *Y, void *stream);
+
+typedef struct {
+  int32_t nrows, ncols;
+  int64_t nnz;
+  const int32_t *rowptr;   /* device */
+  const int16_t *off;      /* device */
+  const void *val;         /* device, dtype of the batch */
+  const void *X;           /* device, row-major ncols x k */
+  void *Y;                 /* device, row-major nrows x k */
+} damn_mat_desc;
+
+typedef struct damn_batch_plan damn_batch_plan;
+
+typedef struct {
+  int32_t count, k, dtype, ntiles, grid, threads, tile_items, graph_ready;
+  double tune_ms;          /* best time measured by the autotuner (0 if none) */
+} damn_batch_desc;
+
+/* Builds the work list of a batch of independent DA-CSR-16 products
+ * Y_m = A_m X_m (host descriptors, device data).  autotune != 0 times the
+ * candidate tilings on the real operands (Y is overwritten) and keeps the
+ * fastest, then captures the persistent launch in a CUDA graph.
+ * Synchronises stream.  The plan owns device memory until destroyed. */
+int damn_batch_plan_create(int32_t count, const damn_mat_desc *h_descs, int32_t k, int dtype,
+                           int autotune, void *stream, damn_batch_plan **out);
+int damn_batch_plan_describe(const damn_batch_plan *plan, damn_batch_desc *h_desc);
+int damn_batch_plan_destroy(damn_batch_plan *plan);
+
+/* One persistent launch computing every Y_m of the batch. */
+int damn_spmm_dacsr16_batched(const damn_batch_plan *plan, void *stream);
+
+/* Replays the CUDA graph captured by damn_batch_plan_create on stream. */
+int damn_batch_graph_launch(damn_batch_plan *plan, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DAMN_H */

@@ -1,0 +1,115 @@
+// Library-wide host state: error messages, the device status word, the
+// failure-detection self test, version.
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+
+#include "damn_common.cuh"
+
+namespace damn {
+
+namespace {
+thread_local std::string g_last_error;
+
+// One status word per device context (a kernel whose bounded wait gives up
+// records DAMN_ERR_TIMEOUT here instead of hanging).
+__device__ int g_status_word;
+
+constexpr int kMaxDevices = 64;
+int *g_status_ptr[kMaxDevices];
+int g_sm_count[kMaxDevices];
+std::mutex g_mu;
+}  // namespace
+
+int set_error(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char *what) {
+  return set_error(DAMN_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int *device_status_ptr() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_status_ptr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+    g_status_ptr[dev] = static_cast<int *>(p);
+  }
+  return g_status_ptr[dev];
+}
+
+int sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_sm_count[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_sm_count[dev] = n > 0 ? n : 1;
+  }
+  return g_sm_count[dev];
+}
+
+// A barrier that nothing ever completes: the bounded wait must give up.
+__global__ void k_selftest_wait(int *status, uint64_t timeout_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0, status, timeout_ns);
+}
+
+}  // namespace damn
+
+using namespace damn;
+
+extern "C" const char *damn_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int damn_version(void) { return 100; }
+
+extern "C" int damn_device_status(int32_t *h_status, int reset, void *stream) {
+  if (!h_status) return set_error(DAMN_ERR_INVALID_ARG, "damn_device_status: h_status is NULL");
+  int *p = device_status_ptr();
+  if (!p) return set_error(DAMN_ERR_CUDA, "damn_device_status: no device status word");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  DAMN_CUDA(cudaMemcpyAsync(&v, p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DAMN_CUDA(cudaStreamSynchronize(s));
+  if (reset) {
+    DAMN_CUDA(cudaMemsetAsync(p, 0, sizeof(int), s));
+    DAMN_CUDA(cudaStreamSynchronize(s));
+  }
+  *h_status = v;
+  return DAMN_OK;
+}
+
+extern "C" int damn_selftest_wait_timeout(int64_t timeout_ns, void *stream) {
+  if (timeout_ns < 1000 || timeout_ns > 10000000000ll)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_selftest_wait_timeout: timeout_ns out of range");
+  int *p = device_status_ptr();
+  if (!p) return set_error(DAMN_ERR_CUDA, "damn_selftest_wait_timeout: no device status word");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DAMN_CUDA(cudaMemsetAsync(p, 0, sizeof(int), s));
+  k_selftest_wait<<<1, 32, 0, s>>>(p, static_cast<uint64_t>(timeout_ns));
+  DAMN_CHECK_LAUNCH("k_selftest_wait");
+  int v = 0;
+  DAMN_CUDA(cudaMemcpyAsync(&v, p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DAMN_CUDA(cudaStreamSynchronize(s));
+  DAMN_CUDA(cudaMemsetAsync(p, 0, sizeof(int), s));
+  DAMN_CUDA(cudaStreamSynchronize(s));
+  if (v == DAMN_ERR_TIMEOUT)
+    return set_error(DAMN_ERR_TIMEOUT, "bounded device wait gave up after %lld ns (expected)",
+                     static_cast<long long>(timeout_ns));
+  return set_error(DAMN_ERR_CUDA, "self test: the wait did not report a timeout (status %d)", v);
+}

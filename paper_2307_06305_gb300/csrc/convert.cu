@@ -1,0 +1,246 @@
+// CSR -> DA-CSR-16 translation with the 16-bit fit check (Section 2,
+// Example 1, Eq. (2)), CSR validation, and round-to-nearest value casts.
+//
+// Each CTA owns a block of kRowsPerBlock rows: it stages their row pointers
+// in shared memory and walks the block's entries with coalesced loads of col
+// and coalesced stores of off, finding each entry's row by binary search in
+// shared memory.  Per-entry work is an int32 subtraction, a narrowing store
+// and min/max/count reductions; the kernel is bound by HBM traffic (4 bytes
+// read + 2 bytes written per entry, plus 4 bytes per row).
+#include <algorithm>
+#include <climits>
+
+#include "damn_common.cuh"
+
+namespace damn {
+namespace {
+
+constexpr int kConvThreads = 256;
+constexpr int kRowsPerBlock = 512;
+
+struct FitAccum {
+  int min_off;
+  int max_off;
+  unsigned long long n_fit;
+  unsigned long long n_bad;
+};
+
+__global__ void k_fit_init(FitAccum *acc) {
+  acc->min_off = INT_MAX;
+  acc->max_off = INT_MIN;
+  acc->n_fit = 0;
+  acc->n_bad = 0;
+}
+
+// Largest local row lr in [0, nr) with rp[lr] <= k (rows are non-empty at k).
+__device__ __forceinline__ int row_of(const int *rp, int nr, int k) {
+  int lo = 0, hi = nr - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (rp[mid] <= k) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_reduce_fit(int mn, int mx, unsigned long long nf,
+                                                 unsigned long long nb, FitAccum *acc) {
+  __shared__ int s_mn[NT / 32], s_mx[NT / 32];
+  __shared__ unsigned long long s_nf[NT / 32], s_nb[NT / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    nf += __shfl_xor_sync(0xffffffffu, nf, o);
+    nb += __shfl_xor_sync(0xffffffffu, nb, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { s_mn[w] = mn; s_mx[w] = mx; s_nf[w] = nf; s_nb[w] = nb; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < NT / 32; ++i) {
+      mn = min(mn, s_mn[i]); mx = max(mx, s_mx[i]); nf += s_nf[i]; nb += s_nb[i];
+    }
+    if (mn != INT_MAX) {
+      atomicMin(&acc->min_off, mn);
+      atomicMax(&acc->max_off, mx);
+    }
+    if (nf) atomicAdd(&acc->n_fit, nf);
+    if (nb) atomicAdd(&acc->n_bad, nb);
+  }
+}
+
+__global__ void __launch_bounds__(kConvThreads)
+k_csr_to_dacsr16(int nrows, int ncols, const int *__restrict__ rowptr, const int *__restrict__ col,
+                 int16_t *__restrict__ off, FitAccum *acc) {
+  __shared__ int rp[kRowsPerBlock + 1];
+  const int r0 = blockIdx.x * kRowsPerBlock;
+  const int nr = min(kRowsPerBlock, nrows - r0);
+  for (int i = threadIdx.x; i <= nr; i += kConvThreads) rp[i] = rowptr[r0 + i];
+  __syncthreads();
+  const int k0 = rp[0], k1 = rp[nr];
+  int mn = INT_MAX, mx = INT_MIN;
+  unsigned long long nf = 0, nb = 0;
+  for (int k = k0 + threadIdx.x; k < k1; k += kConvThreads) {
+    const int lr = row_of(rp, nr, k);
+    const int c = __ldcs(col + k);
+    const int d = c - (r0 + lr);  // |d| < 2^31 since 0 <= r, c < 2^31
+    __stcs(off + k, static_cast<int16_t>(d));
+    mn = min(mn, d);
+    mx = max(mx, d);
+    nf += (d >= -32768 && d <= 32767) ? 1ull : 0ull;
+    nb += (c < 0 || c >= ncols) ? 1ull : 0ull;
+  }
+  block_reduce_fit<kConvThreads>(mn, mx, nf, nb, acc);
+}
+
+struct ValidateAccum {
+  unsigned long long bad_rows;
+  unsigned long long bad_cols;
+};
+
+__global__ void k_validate(int nrows, int ncols, long long nnz, const int *__restrict__ rowptr,
+                           const int *__restrict__ col, ValidateAccum *acc) {
+  unsigned long long br = 0, bc = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (long long r = tid; r < nrows; r += stride) br += rowptr[r] > rowptr[r + 1] ? 1 : 0;
+  if (tid == 0) br += (rowptr[0] != 0 ? 1 : 0) + ((long long)rowptr[nrows] != nnz ? 1 : 0);
+  for (long long k = tid; k < nnz; k += stride) {
+    const int c = col[k];
+    bc += (c < 0 || c >= ncols) ? 1 : 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    br += __shfl_xor_sync(0xffffffffu, br, o);
+    bc += __shfl_xor_sync(0xffffffffu, bc, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (br) atomicAdd(&acc->bad_rows, br);
+    if (bc) atomicAdd(&acc->bad_cols, bc);
+  }
+}
+
+// Round-to-nearest-even narrowing written from the IEEE 754 encodings:
+// the significand is cut to 8 bits (bfloat16) with the discarded bits
+// compared against one half ulp; values below 2^-126 become bfloat16
+// subnormals (spacing 2^-133); overflow becomes infinity.
+__device__ __forceinline__ uint16_t bf16_bits_from_double(double v) {
+  const unsigned long long b = __double_as_longlong(v);
+  const uint16_t sign = static_cast<uint16_t>((b >> 48) & 0x8000u);
+  const int ef = static_cast<int>((b >> 52) & 0x7ff);
+  const unsigned long long frac = b & ((1ull << 52) - 1);
+  if (ef == 0x7ff) return frac ? static_cast<uint16_t>(sign | 0x7fc0u) : static_cast<uint16_t>(sign | 0x7f80u);
+  if (ef == 0) return sign;  // FP64 zero or subnormal (< 2^-1022): rounds to zero
+  const int e = ef - 1023;
+  const unsigned long long m = (1ull << 52) | frac;  // 53-bit significand
+  int shift = 45;                                    // keep 8 bits for normals
+  if (e < -126) shift += (-126 - e);                 // fewer bits for subnormals
+  if (shift > 60) return sign;                       // far below half the smallest subnormal
+  unsigned long long q = m >> shift;
+  const unsigned long long rem = m & ((1ull << shift) - 1);
+  const unsigned long long half = 1ull << (shift - 1);
+  if (rem > half || (rem == half && (q & 1ull))) ++q;
+  if (e < -126) return static_cast<uint16_t>(sign | q);  // q <= 128: 128 is the smallest normal
+  int eb = e + 127;
+  if (q == 256) { q = 128; ++eb; }
+  if (eb >= 255) return static_cast<uint16_t>(sign | 0x7f80u);
+  return static_cast<uint16_t>(sign | (eb << 7) | (q & 127u));
+}
+
+__global__ void k_cast(long long n, const void *src, int st, void *dst, int dt) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double v = (st == DAMN_F64) ? static_cast<const double *>(src)[i]
+                                      : static_cast<double>(static_cast<const float *>(src)[i]);
+    if (dt == DAMN_F32)
+      static_cast<float *>(dst)[i] = __double2float_rn(v);
+    else
+      static_cast<uint16_t *>(dst)[i] = bf16_bits_from_double(v);
+  }
+}
+
+}  // namespace
+}  // namespace damn
+
+using namespace damn;
+
+extern "C" size_t damn_csr_to_dacsr_workspace_size(void) { return 256; }
+
+extern "C" int damn_csr_to_dacsr(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                                 const int32_t *col, int16_t *off_out, damn_fit_info *h_info,
+                                 void *workspace, size_t ws_bytes, void *stream) {
+  if (nrows < 0 || ncols < 0 || nnz < 0 || nnz > INT_MAX)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_csr_to_dacsr: bad sizes");
+  if (!h_info || !rowptr || (nnz > 0 && (!col || !off_out)))
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_csr_to_dacsr: NULL pointer");
+  if (!workspace || ws_bytes < damn_csr_to_dacsr_workspace_size() || !aligned16(workspace))
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_csr_to_dacsr: workspace too small or misaligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  FitAccum *acc = static_cast<FitAccum *>(workspace);
+  k_fit_init<<<1, 1, 0, s>>>(acc);
+  DAMN_CHECK_LAUNCH("k_fit_init");
+  if (nrows > 0) {
+    const int blocks = (nrows + kRowsPerBlock - 1) / kRowsPerBlock;
+    k_csr_to_dacsr16<<<blocks, kConvThreads, 0, s>>>(nrows, ncols, rowptr, col, off_out, acc);
+    DAMN_CHECK_LAUNCH("k_csr_to_dacsr16");
+  }
+  FitAccum h{};
+  DAMN_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+  DAMN_CUDA(cudaStreamSynchronize(s));
+  if (nnz == 0) { h.min_off = 0; h.max_off = 0; }
+  h_info->min_off = h.min_off;
+  h_info->max_off = h.max_off;
+  h_info->w = std::max<int64_t>(-(int64_t)h.min_off, (int64_t)h.max_off);
+  h_info->n_fit = static_cast<int64_t>(h.n_fit);
+  h_info->n_bad = static_cast<int64_t>(h.n_bad);
+  h_info->fits = (static_cast<int64_t>(h.n_fit) == nnz && h.n_bad == 0) ? 1 : 0;
+  h_info->reserved = 0;
+  if (!h_info->fits)
+    return set_error(DAMN_ERR_NOFIT,
+                     "damn_csr_to_dacsr: %lld of %lld entries do not fit int16 (min %d, max %d), %lld bad columns",
+                     (long long)(nnz - h_info->n_fit), (long long)nnz, h.min_off, h.max_off,
+                     (long long)h.n_bad);
+  return DAMN_OK;
+}
+
+extern "C" size_t damn_validate_csr_workspace_size(void) { return 256; }
+
+extern "C" int damn_validate_csr(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                                 const int32_t *col, int64_t *h_bad_rows, int64_t *h_bad_cols,
+                                 void *workspace, size_t ws_bytes, void *stream) {
+  if (nrows < 0 || ncols < 0 || nnz < 0 || nnz > INT_MAX)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_validate_csr: bad sizes");
+  if (!rowptr || (nnz > 0 && !col) || !h_bad_rows || !h_bad_cols)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_validate_csr: NULL pointer");
+  if (!workspace || ws_bytes < damn_validate_csr_workspace_size() || !aligned16(workspace))
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_validate_csr: workspace too small or misaligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ValidateAccum *acc = static_cast<ValidateAccum *>(workspace);
+  DAMN_CUDA(cudaMemsetAsync(acc, 0, sizeof(ValidateAccum), s));
+  const int blocks = std::max(1, std::min(4 * sm_count(), (int)((std::max<int64_t>(nnz, nrows) + 255) / 256)));
+  k_validate<<<blocks, 256, 0, s>>>(nrows, ncols, nnz, rowptr, col, acc);
+  DAMN_CHECK_LAUNCH("k_validate");
+  ValidateAccum h{};
+  DAMN_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+  DAMN_CUDA(cudaStreamSynchronize(s));
+  *h_bad_rows = static_cast<int64_t>(h.bad_rows);
+  *h_bad_cols = static_cast<int64_t>(h.bad_cols);
+  if (h.bad_rows || h.bad_cols)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_validate_csr: %llu bad row pointers, %llu bad columns",
+                     h.bad_rows, h.bad_cols);
+  return DAMN_OK;
+}
+
+extern "C" int damn_cast_values(int64_t n, const void *src, int src_dtype, void *dst, int dst_dtype,
+                                void *stream) {
+  if (n < 0) return set_error(DAMN_ERR_INVALID_ARG, "damn_cast_values: n < 0");
+  if (n == 0) return DAMN_OK;
+  if (!src || !dst) return set_error(DAMN_ERR_INVALID_ARG, "damn_cast_values: NULL pointer");
+  const bool ok = (src_dtype == DAMN_F64 && (dst_dtype == DAMN_F32 || dst_dtype == DAMN_BF16)) ||
+                  (src_dtype == DAMN_F32 && dst_dtype == DAMN_BF16);
+  if (!ok) return set_error(DAMN_ERR_UNSUPPORTED, "damn_cast_values: unsupported dtype pair");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int blocks = (int)std::min<int64_t>(8LL * sm_count(), (n + 255) / 256);
+  k_cast<<<blocks, 256, 0, s>>>(n, src, src_dtype, dst, dst_dtype);
+  DAMN_CHECK_LAUNCH("k_cast");
+  return DAMN_OK;
+}

@@ -1,0 +1,612 @@
+// SpMV entry points, plans and launch plumbing.  The kernels are in
+// spmv_kernel.cuh; see there for the design.
+//
+// A plan fixes, for one matrix: the tile partition (fixed row blocks, or
+// blocks balanced on rows + entries), the compute mode (one row per thread or
+// balanced slices), and, when the column indices are given, the x window of
+// every tile -- the sorted distinct columns of the tile clustered into at most
+// four contiguous segments (gaps of up to kXGap columns merged, then the
+// closest segments merged until four remain) that the
+// producer stages into shared memory with the matrix data.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "damn_common.cuh"
+#include "spmv_internal.h"
+#include "spmv_kernel.cuh"
+
+using namespace damn::spmvk;
+
+namespace damn {
+namespace {
+
+constexpr int kMaxDev = 64;
+constexpr int kRowWeight = 4;       // merge-path weight of a row against an entry
+constexpr int kBalancedItems = 2048;
+constexpr int kXGap = 32;           // columns: smaller gaps are staged, not split
+
+// ----------------------------------------------------------------------------
+// Launch
+// ----------------------------------------------------------------------------
+template <bool PLAIN, typename V, typename I, class C>
+int launch_kernel(SpmvParams p, cudaStream_t s, int *gs_out) {
+  using L = Layout<V, I, C>;
+  // per device and mode: chosen ring depth and CTAs per SM (0 = not yet known)
+  static int stages_of[kMaxDev][2], occ_of[kMaxDev][2];
+  static std::mutex mu;
+  int dev = 0;
+  DAMN_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) return set_error(DAMN_ERR_UNSUPPORTED, "device index too large");
+  const int mode = p.mode == 1 ? 1 : 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!occ_of[dev][mode]) {
+      int max_optin = 0;
+      DAMN_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      DAMN_CUDA(cudaFuncSetAttribute(k_spmv<PLAIN, V, I, C>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin));
+      // deepest ring that keeps two CTAs per SM (at least two stages)
+      int best_s = 2, best_o = 0;
+      for (int st = kMaxStages; st >= 2; --st) {
+        if (L::total(st, mode) > (size_t)max_optin) continue;
+        int o = 0;
+        DAMN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_spmv<PLAIN, V, I, C>,
+                                                                C::NT + 32, L::total(st, mode)));
+        if (o >= 2) { best_s = st; best_o = o; break; }
+        if (o > best_o) { best_s = st; best_o = o; }
+      }
+      stages_of[dev][mode] = best_s;
+      occ_of[dev][mode] = std::max(1, best_o);
+    }
+  }
+  p.stages = stages_of[dev][mode];
+  const int grid = std::max(1, std::min(p.ntiles, occ_of[dev][mode] * sm_count()));
+  if (gs_out) { gs_out[0] = grid; gs_out[1] = p.stages; }
+  if (p.ntiles == 0) return DAMN_OK;
+  k_spmv<PLAIN, V, I, C><<<grid, C::NT + 32, L::total(p.stages, mode), s>>>(p);
+  DAMN_CHECK_LAUNCH("k_spmv");
+  return DAMN_OK;
+}
+
+template <typename V, typename I, class C>
+int launch_cfg(const SpmvParams &p, cudaStream_t s, int *gs) {
+  const bool plain = p.ab_mode == 0 && !p.dot_w && !p.dot_self && !p.dot_partials;
+  if (plain) return launch_kernel<true, V, I, C>(p, s, gs);
+  return launch_kernel<false, V, I, C>(p, s, gs);
+}
+
+template <typename V, typename I>
+int launch_types(const SpmvParams &p, int shape, cudaStream_t s, int *gs) {
+  if (shape == 1) return launch_cfg<V, I, Cfg128>(p, s, gs);
+  return launch_cfg<V, I, Cfg224>(p, s, gs);
+}
+
+int launch_any(const SpmvParams &p, int dtype, int fmt, int shape, cudaStream_t s, int *gs) {
+  if (fmt == DAMN_FMT_DACSR16) {
+    if (dtype == DAMN_F64) return launch_types<double, int16_t>(p, shape, s, gs);
+    if (dtype == DAMN_F32) return launch_types<float, int16_t>(p, shape, s, gs);
+    return launch_types<__nv_bfloat16, int16_t>(p, shape, s, gs);
+  }
+  if (dtype == DAMN_F64) return launch_types<double, int32_t>(p, shape, s, gs);
+  if (dtype == DAMN_F32) return launch_types<float, int32_t>(p, shape, s, gs);
+  return launch_types<__nv_bfloat16, int32_t>(p, shape, s, gs);
+}
+
+// ----------------------------------------------------------------------------
+// Plan kernels
+// ----------------------------------------------------------------------------
+
+// Tile t starts at the first row r with kRowWeight * r + rowptr[r] >= t * D.
+__global__ void k_plan_bounds(int nrows, const int *__restrict__ rowptr, long long D, int ntiles,
+                              int2 *bounds) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > ntiles) return;
+  int r;
+  if (t == ntiles) {
+    r = nrows;
+  } else {
+    const long long target = (long long)t * D;
+    int lo = 0, hi = nrows;
+    while (lo < hi) {
+      const int mid = lo + ((hi - lo) >> 1);
+      if ((long long)kRowWeight * mid + rowptr[mid] >= target) hi = mid; else lo = mid + 1;
+    }
+    r = lo;
+  }
+  bounds[t] = make_int2(r, rowptr[r]);
+}
+
+struct PlanStats {
+  unsigned long long sum_group_max;  // sum over 32-row groups of the longest row
+  int max_row;
+  int max_tile_short;                // most entries in a Cfg224::NT-row tile
+  int max_tile_long;                 // most entries in a Cfg128::NT-row tile
+  int pad;
+};
+
+__global__ void k_plan_stats(int nrows, const int *__restrict__ rowptr, PlanStats *st) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int len = 0;
+  if (i < nrows) len = rowptr[i + 1] - rowptr[i];
+  int gmax = len;
+  for (int o = 16; o > 0; o >>= 1) gmax = max(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&st->sum_group_max, (unsigned long long)gmax);
+    atomicMax(&st->max_row, gmax);
+  }
+  if (i < nrows && i % Cfg224::NT == 0) {
+    const int r1 = (int)min((long long)nrows, i + Cfg224::NT);
+    atomicMax(&st->max_tile_short, rowptr[r1] - rowptr[i]);
+  }
+  if (i < nrows && i % Cfg128::NT == 0) {
+    const int r1 = (int)min((long long)nrows, i + Cfg128::NT);
+    atomicMax(&st->max_tile_long, rowptr[r1] - rowptr[i]);
+  }
+}
+
+constexpr int kXSortCap = 4096;  // >= every CAP_NZ
+constexpr int kXRowsCap = 513;   // >= every CAP_ROWS + 1
+constexpr int kXStartCap = 64;   // segment starts considered for merging
+
+// x window of every tile: columns of the tile's entries, sorted (bitonic, in
+// shared memory), cut where consecutive columns differ by more than kXGap.
+// A tile gets a window when it has at most kXSegMax segments whose 16-byte
+// aligned lengths (ex elements per 16 bytes) add up to at most xcap elements;
+// otherwise nseg = 0 and the kernel gathers x from global memory.
+__global__ void __launch_bounds__(256)
+k_plan_xseg(int nrows, int ncols, const int *__restrict__ rowptr, const void *idx, int fmt,
+            int ntiles, int rows_per_tile, const int2 *__restrict__ bounds, int cap_nz, int xcap,
+            int ex, XSeg *out) {
+  __shared__ int keys[kXSortCap];
+  __shared__ int rps[kXRowsCap];
+  __shared__ int bpos[kXStartCap];
+  __shared__ int nb;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int r0, r1, k0, k1;
+    if (rows_per_tile > 0) {
+      r0 = t * rows_per_tile;
+      r1 = min(r0 + rows_per_tile, nrows);
+      k0 = rowptr[r0];
+      k1 = rowptr[r1];
+    } else {
+      const int2 b0 = bounds[t], b1 = bounds[t + 1];
+      r0 = b0.x; k0 = b0.y; r1 = b1.x; k1 = b1.y;
+    }
+    const int m = k1 - k0, nr = r1 - r0;
+    if (m == 0 || m > cap_nz || m > kXSortCap || nr + 1 > kXRowsCap) {
+      if (threadIdx.x == 0) out[t].nseg = 0;
+      continue;  // uniform across the block
+    }
+    for (int i = threadIdx.x; i <= nr; i += blockDim.x) rps[i] = rowptr[r0 + i];
+    if (threadIdx.x == 0) nb = 0;
+    __syncthreads();
+    int P = 1;
+    while (P < m) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+      int c = INT_MAX;
+      if (i < m) {
+        const int k = k0 + i;
+        if (fmt == DAMN_FMT_CSR32) {
+          c = static_cast<const int *>(idx)[k];
+        } else {
+          int lo = 0, hi = nr - 1;  // last local row with rps[row] <= k
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (rps[mid] <= k) lo = mid; else hi = mid - 1;
+          }
+          c = r0 + lo + static_cast<int>(static_cast<const int16_t *>(idx)[k]);
+        }
+      }
+      keys[i] = c;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+          const int jx = i ^ stride;
+          if (jx > i) {
+            const bool up = (i & size) == 0;
+            const int a = keys[i], b = keys[jx];
+            if ((a > b) == up) { keys[i] = b; keys[jx] = a; }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // Runs of columns separated by more than kXGap start a new segment; while
+    // there are more than kXSegMax segments, the two neighbours with the
+    // smallest gap are merged (thread 0; the starts are few).
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      if (i == 0 || keys[i] - keys[i - 1] > kXGap) {
+        const int slot = atomicAdd(&nb, 1);
+        if (slot < kXStartCap) bpos[slot] = i;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int n = nb;
+      XSeg seg;
+      seg.nseg = 0;
+      if (n <= kXStartCap) {
+        for (int a = 1; a < n; ++a) {  // insertion sort of the starts
+          const int v = bpos[a];
+          int b = a - 1;
+          while (b >= 0 && bpos[b] > v) { bpos[b + 1] = bpos[b]; --b; }
+          bpos[b + 1] = v;
+        }
+        while (n > kXSegMax) {  // merge across the smallest gap
+          int best = 1, bg = INT_MAX;
+          for (int a = 1; a < n; ++a) {
+            const int g = keys[bpos[a]] - keys[bpos[a] - 1];
+            if (g < bg) { bg = g; best = a; }
+          }
+          for (int a = best; a + 1 < n; ++a) bpos[a] = bpos[a + 1];
+          --n;
+        }
+        // staging layout: segment a is copied from its 16-byte aligned start
+        // src to slot dst (running sum of aligned lengths); x must hold every
+        // copied element (no partial block at the end of x).
+        long long total = 0;
+        bool fits = true;
+        const long long x_full = (long long)ncols & ~(long long)(ex - 1);
+        for (int a = 0; a < n; ++a) {
+          const int first = bpos[a];
+          const int lastpos = (a + 1 < n ? bpos[a + 1] : m) - 1;
+          const int lo = keys[first], hi = keys[lastpos] + 1;
+          const long long a0 = lo & ~(long long)(ex - 1);
+          const long long a1 = ((long long)hi + ex - 1) & ~(long long)(ex - 1);
+          if (a1 > x_full) fits = false;
+          seg.lo[a] = lo;
+          seg.src[a] = static_cast<int>(a0);
+          seg.cnt[a] = static_cast<int>(a1 - a0);
+          seg.pos[a] = static_cast<int>(total + (lo - a0));
+          total += a1 - a0;
+        }
+        if (fits && total <= xcap) seg.nseg = n;
+      }
+      for (int a = seg.nseg; a < kXSegMax; ++a) {
+        seg.lo[a] = 0; seg.pos[a] = 0; seg.src[a] = 0; seg.cnt[a] = 0;
+      }
+      seg.pad[0] = seg.pad[1] = seg.pad[2] = 0;
+      out[t] = seg;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_count_staged(const XSeg *xs, int ntiles, int *count) {
+  int c = 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
+    c += xs[t].nseg > 0 ? 1 : 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+}  // namespace
+}  // namespace damn
+
+struct damn_plan {
+  int nrows, ncols;
+  long long nnz;
+  int dtype;
+  const int32_t *rowptr;  // caller's arrays (kept for the autotuner and the x windows)
+  const void *idx;        // column indices (may be NULL: no x windows)
+  int fmt;
+  int mode;               // 0 rows per thread, 1 balanced slices
+  int shape;              // 0: Cfg224, 1: Cfg128
+  int rows_per_tile;      // > 0 fixed row tiles, 0 bounds
+  int ntiles;
+  int2 *d_bounds;         // bounds of the current tiling (NULL for fixed rows)
+  int2 *d_bounds_balanced;
+  int ntiles_balanced;
+  XSeg *d_xseg;           // x windows of the current tiling (NULL: none)
+  int xseg_cap;
+  int staged_tiles;
+  int max_row;
+  double row_eff;
+  int max_tile_short, max_tile_long;
+  int grid, stages;       // geometry of the last launch
+};
+
+namespace damn {
+
+int spmv_max_grid() { return 8 * sm_count(); }
+
+static int make_params(const SpmvCall &c, const damn_plan *plan, SpmvParams &p, int &shape) {
+  std::memset(&p, 0, sizeof(p));
+  p.nrows = c.nrows;
+  p.ncols = c.ncols;
+  p.nnz = c.nnz;
+  p.rowptr = c.rowptr;
+  p.idx = c.idx;
+  p.val = c.val;
+  p.x = c.x;
+  p.y0 = c.y0 ? c.y0 : c.y;
+  p.y = c.y;
+  p.alpha = c.alpha;
+  p.beta = c.beta;
+  p.ab_mode = (c.beta != 0.0) ? 2 : (c.alpha == 1.0 ? 0 : 1);
+  p.dot_w = c.dot_w;
+  p.dot_self = c.dot_self;
+  p.dot_partials = c.dot_partials;
+  p.status = device_status_ptr();
+  p.timeout_ns = kWaitTimeoutNs;
+  if (!p.status) return set_error(DAMN_ERR_CUDA, "no device status word");
+  if (plan) {
+    p.mode = plan->mode;
+    p.rows_per_tile = plan->rows_per_tile;
+    p.ntiles = plan->ntiles;
+    p.bounds = plan->d_bounds;
+    p.xseg = plan->d_xseg;
+    shape = plan->shape;
+  } else {
+    p.mode = 1;
+    p.rows_per_tile = 256;
+    p.ntiles = (c.nrows + 255) / 256;
+    p.bounds = nullptr;
+    p.xseg = nullptr;
+    shape = 0;
+  }
+  return DAMN_OK;
+}
+
+int spmv_launch(const SpmvCall &c, const damn_plan *plan, cudaStream_t s, int *grid_out) {
+  SpmvParams p;
+  int shape = 0;
+  int rc = make_params(c, plan, p, shape);
+  if (rc) return rc;
+  int gs[2] = {0, 0};
+  rc = launch_any(p, c.dtype, c.fmt, shape, s, gs);
+  if (grid_out) *grid_out = gs[0];
+  if (plan && rc == DAMN_OK) {
+    // launch geometry is reported by damn_plan_describe
+    const_cast<damn_plan *>(plan)->grid = gs[0];
+    const_cast<damn_plan *>(plan)->stages = gs[1];
+  }
+  return rc;
+}
+
+}  // namespace damn
+
+using namespace damn;
+
+static int check_spmv_args(const char *fn, int32_t nrows, int32_t ncols, int64_t nnz,
+                           const int32_t *rowptr, const void *idx, const void *val, int dtype,
+                           const void *x, void *y, const damn_plan *plan) {
+  if (nrows < 0 || ncols < 0 || nnz < 0 || nnz > INT_MAX)
+    return set_error(DAMN_ERR_INVALID_ARG, "%s: bad sizes", fn);
+  if (dtype != DAMN_F64 && dtype != DAMN_F32 && dtype != DAMN_BF16)
+    return set_error(DAMN_ERR_INVALID_ARG, "%s: bad dtype %d", fn, dtype);
+  if (nrows > 0 && (!rowptr || !y)) return set_error(DAMN_ERR_INVALID_ARG, "%s: NULL pointer", fn);
+  if (nnz > 0 && (!idx || !val || !x)) return set_error(DAMN_ERR_INVALID_ARG, "%s: NULL pointer", fn);
+  if (!aligned16(rowptr) || !aligned16(idx) || !aligned16(val) || !aligned16(x) || !aligned16(y))
+    return set_error(DAMN_ERR_INVALID_ARG, "%s: pointers must be 16-byte aligned", fn);
+  if (plan && (plan->nrows != nrows || plan->ncols != ncols || plan->nnz != nnz ||
+               plan->dtype != dtype))
+    return set_error(DAMN_ERR_INVALID_ARG, "%s: plan was built for another matrix or dtype", fn);
+  return DAMN_OK;
+}
+
+static int spmv_entry(const char *fn, int fmt, int32_t nrows, int32_t ncols, int64_t nnz,
+                      const int32_t *rowptr, const void *idx, const void *val, int dtype,
+                      const void *x, void *y, double alpha, double beta, const damn_plan *plan,
+                      void *stream) {
+  int rc = check_spmv_args(fn, nrows, ncols, nnz, rowptr, idx, val, dtype, x, y, plan);
+  if (rc) return rc;
+  if (nrows == 0) return DAMN_OK;
+  SpmvCall c;
+  c.nrows = nrows; c.ncols = ncols; c.nnz = nnz; c.rowptr = rowptr; c.idx = idx; c.fmt = fmt;
+  c.val = val; c.dtype = dtype; c.x = x; c.y0 = y; c.y = y; c.alpha = alpha; c.beta = beta;
+  return spmv_launch(c, plan, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+extern "C" int damn_spmv_csr32(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                               const int32_t *col, const void *val, int dtype, const void *x,
+                               void *y, double alpha, double beta, const damn_plan *plan,
+                               void *stream) {
+  return spmv_entry("damn_spmv_csr32", DAMN_FMT_CSR32, nrows, ncols, nnz, rowptr, col, val, dtype,
+                    x, y, alpha, beta, plan, stream);
+}
+
+extern "C" int damn_spmv_dacsr16(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                                 const int16_t *off, const void *val, int dtype, const void *x,
+                                 void *y, double alpha, double beta, const damn_plan *plan,
+                                 void *stream) {
+  return spmv_entry("damn_spmv_dacsr16", DAMN_FMT_DACSR16, nrows, ncols, nnz, rowptr, off, val,
+                    dtype, x, y, alpha, beta, plan, stream);
+}
+
+// ----------------------------------------------------------------------------
+// Plans
+// ----------------------------------------------------------------------------
+static void plan_free_device(damn_plan *pl) {
+  if (pl->d_bounds_balanced) cudaFree(pl->d_bounds_balanced);
+  if (pl->d_xseg) cudaFree(pl->d_xseg);
+  pl->d_bounds_balanced = nullptr;
+  pl->d_xseg = nullptr;
+  pl->d_bounds = nullptr;
+}
+
+// Recomputes the x windows for the plan's current tiling (synchronises).
+static int plan_xwindows(damn_plan *pl, cudaStream_t s) {
+  pl->staged_tiles = 0;
+  if (!pl->idx || pl->ntiles == 0 || pl->nrows == 0) return DAMN_OK;
+  if (pl->xseg_cap < pl->ntiles) {
+    if (pl->d_xseg) cudaFree(pl->d_xseg);
+    pl->d_xseg = nullptr;
+    pl->xseg_cap = 0;
+    DAMN_CUDA(cudaMalloc(&pl->d_xseg, sizeof(XSeg) * (size_t)pl->ntiles));
+    pl->xseg_cap = pl->ntiles;
+  }
+  const int asz = pl->dtype == DAMN_F64 ? 8 : 4;
+  const int cap_nz = pl->shape == 1 ? Cfg128::CAP_NZ : Cfg224::CAP_NZ;
+  const int xbytes = pl->shape == 1 ? Cfg128::XBYTES : Cfg224::XBYTES;
+  const int blocks = std::min(pl->ntiles, 16 * sm_count());
+  k_plan_xseg<<<blocks, 256, 0, s>>>(pl->nrows, pl->ncols, pl->rowptr, pl->idx, pl->fmt, pl->ntiles,
+                                     pl->rows_per_tile, pl->d_bounds, cap_nz, xbytes / asz,
+                                     16 / asz, pl->d_xseg);
+  DAMN_CHECK_LAUNCH("k_plan_xseg");
+  int *d_cnt = nullptr;
+  DAMN_CUDA(cudaMallocAsync(&d_cnt, sizeof(int), s));
+  DAMN_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int), s));
+  k_count_staged<<<std::min(1024, (pl->ntiles + 255) / 256), 256, 0, s>>>(pl->d_xseg, pl->ntiles,
+                                                                          d_cnt);
+  int h = 0;
+  DAMN_CUDA(cudaMemcpyAsync(&h, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DAMN_CUDA(cudaFreeAsync(d_cnt, s));
+  DAMN_CUDA(cudaStreamSynchronize(s));
+  pl->staged_tiles = h;
+  return DAMN_OK;
+}
+
+static int plan_use(damn_plan *pl, int tiling, cudaStream_t s) {
+  if (tiling == DAMN_TILING_SLICES) {
+    pl->mode = 1;
+    pl->shape = 0;
+    pl->rows_per_tile = 0;
+    pl->ntiles = pl->ntiles_balanced;
+    pl->d_bounds = pl->d_bounds_balanced;
+  } else {
+    const int shape = tiling == DAMN_TILING_ROWS_LONG ? 1 : 0;
+    pl->mode = 0;
+    pl->shape = shape;
+    pl->rows_per_tile = shape == 1 ? Cfg128::NT : Cfg224::NT;
+    pl->ntiles = (pl->nrows + pl->rows_per_tile - 1) / pl->rows_per_tile;
+    pl->d_bounds = nullptr;
+  }
+  return plan_xwindows(pl, s);
+}
+
+static int plan_tiling_of(const damn_plan *pl) {
+  if (pl->mode == 1) return DAMN_TILING_SLICES;
+  return pl->shape == 1 ? DAMN_TILING_ROWS_LONG : DAMN_TILING_ROWS;
+}
+
+extern "C" int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                                int format, const void *idx, int dtype, void *stream,
+                                damn_plan **out) {
+  if (!out) return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_create: out is NULL");
+  *out = nullptr;
+  if (nrows < 0 || ncols < 0 || nnz < 0 || nnz > INT_MAX || (nrows > 0 && !rowptr))
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_create: bad arguments");
+  if (dtype != DAMN_F64 && dtype != DAMN_F32 && dtype != DAMN_BF16)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_create: bad dtype");
+  if (idx && format != DAMN_FMT_CSR32 && format != DAMN_FMT_DACSR16)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_create: bad format");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  damn_plan *pl = new damn_plan();
+  std::memset(pl, 0, sizeof(*pl));
+  pl->nrows = nrows; pl->ncols = ncols; pl->nnz = nnz; pl->dtype = dtype;
+  pl->rowptr = rowptr;
+  pl->idx = nnz > 0 ? idx : nullptr;
+  pl->fmt = format;
+  const long long items = (long long)kRowWeight * nrows + nnz;
+  const long long D = kBalancedItems;
+  pl->ntiles_balanced = (int)((items + D - 1) / D);
+  cudaError_t e = cudaMalloc(&pl->d_bounds_balanced, sizeof(int2) * (pl->ntiles_balanced + 1));
+  if (e != cudaSuccess) { delete pl; return cuda_error(e, "damn_plan_create: cudaMalloc"); }
+  PlanStats *d_st = nullptr;
+  e = cudaMallocAsync(&d_st, sizeof(PlanStats), s);
+  if (e != cudaSuccess) { plan_free_device(pl); delete pl; return cuda_error(e, "cudaMallocAsync"); }
+  cudaMemsetAsync(d_st, 0, sizeof(PlanStats), s);
+  if (nrows > 0) {
+    k_plan_bounds<<<(pl->ntiles_balanced + 1 + 255) / 256, 256, 0, s>>>(
+        nrows, rowptr, D, pl->ntiles_balanced, pl->d_bounds_balanced);
+    k_plan_stats<<<(nrows + 255) / 256, 256, 0, s>>>(nrows, rowptr, d_st);
+  }
+  PlanStats h{};
+  cudaMemcpyAsync(&h, d_st, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d_st, s);
+  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) { plan_free_device(pl); delete pl; return cuda_error(e, "damn_plan_create"); }
+  pl->max_row = h.max_row;
+  pl->max_tile_short = h.max_tile_short;
+  pl->max_tile_long = h.max_tile_long;
+  pl->row_eff = h.sum_group_max ? (double)nnz / (32.0 * (double)h.sum_group_max) : 1.0;
+  // Heuristic choice: one row per thread when rows are uniform inside 32-row
+  // groups and a row block fits a stage; balanced slices otherwise.
+  int tiling = DAMN_TILING_SLICES;
+  if (pl->row_eff >= 0.85 && pl->max_tile_short <= Cfg224::CAP_NZ)
+    tiling = DAMN_TILING_ROWS;
+  else if (pl->row_eff >= 0.85 && pl->max_tile_long <= Cfg128::CAP_NZ)
+    tiling = DAMN_TILING_ROWS_LONG;
+  int rc = plan_use(pl, tiling, s);
+  if (rc) { plan_free_device(pl); delete pl; return rc; }
+  *out = pl;
+  return DAMN_OK;
+}
+
+extern "C" int damn_plan_autotune(damn_plan *plan, int format, const void *idx, const void *val,
+                                  const void *x, void *y, void *stream) {
+  if (!plan) return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_autotune: plan is NULL");
+  if (format != DAMN_FMT_CSR32 && format != DAMN_FMT_DACSR16)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_autotune: bad format");
+  int rc = check_spmv_args("damn_plan_autotune", plan->nrows, plan->ncols, plan->nnz, plan->rowptr,
+                           idx, val, plan->dtype, x, y, plan);
+  if (rc) return rc;
+  if (plan->nrows == 0) return DAMN_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SpmvCall c;
+  c.nrows = plan->nrows; c.ncols = plan->ncols; c.nnz = plan->nnz; c.rowptr = plan->rowptr;
+  c.idx = idx; c.fmt = format; c.val = val; c.dtype = plan->dtype; c.x = x; c.y0 = y; c.y = y;
+  cudaEvent_t e0, e1;
+  DAMN_CUDA(cudaEventCreate(&e0));
+  DAMN_CUDA(cudaEventCreate(&e1));
+  const int cands[3] = {DAMN_TILING_ROWS, DAMN_TILING_ROWS_LONG, DAMN_TILING_SLICES};
+  float best_ms = 1e30f;
+  int best = plan_tiling_of(plan);
+  for (int ci = 0; ci < 3 && rc == DAMN_OK; ++ci) {
+    rc = plan_use(plan, cands[ci], s);
+    for (int w = 0; w < 2 && rc == DAMN_OK; ++w) rc = spmv_launch(c, plan, s, nullptr);
+    float tmin = 1e30f;
+    for (int r = 0; r < 5 && rc == DAMN_OK; ++r) {
+      cudaEventRecord(e0, s);
+      rc = spmv_launch(c, plan, s, nullptr);
+      cudaEventRecord(e1, s);
+      cudaError_t ce = cudaEventSynchronize(e1);
+      if (ce != cudaSuccess) { rc = cuda_error(ce, "damn_plan_autotune"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tmin = std::min(tmin, ms);
+    }
+    if (tmin < best_ms) { best_ms = tmin; best = cands[ci]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  return plan_use(plan, best, s);
+}
+
+extern "C" int damn_plan_set_tiling(damn_plan *plan, int tiling) {
+  if (!plan) return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_set_tiling: plan is NULL");
+  if (tiling != DAMN_TILING_SLICES && tiling != DAMN_TILING_ROWS && tiling != DAMN_TILING_ROWS_LONG)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_set_tiling: bad tiling %d", tiling);
+  return plan_use(plan, tiling, nullptr);
+}
+
+extern "C" int damn_plan_describe(const damn_plan *plan, damn_plan_desc *h_desc) {
+  if (!plan || !h_desc) return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_describe: NULL");
+  h_desc->mode = plan->mode;
+  h_desc->tile_items = plan->rows_per_tile > 0 ? plan->rows_per_tile : kBalancedItems;
+  h_desc->ntiles = plan->ntiles;
+  h_desc->grid = plan->grid;
+  h_desc->stages = plan->stages;
+  h_desc->threads = plan->shape == 1 ? Cfg128::NT : Cfg224::NT;
+  h_desc->row_efficiency = plan->row_eff;
+  h_desc->max_row = plan->max_row;
+  h_desc->dtype = plan->dtype;
+  h_desc->tiling = plan_tiling_of(plan);
+  h_desc->x_staged_tiles = plan->staged_tiles;
+  return DAMN_OK;
+}
+
+extern "C" int damn_plan_destroy(damn_plan *plan) {
+  if (!plan) return DAMN_OK;
+  plan_free_device(plan);
+  delete plan;
+  return DAMN_OK;
+}

@@ -1,0 +1,650 @@
+// Device side of the SpMV engine: y <- alpha A x + beta y for CSR-32 and
+// DA-CSR-16 (Section 4, Listing 2) with FP64 values, or FP32 / BF16 values
+// with FP32 vectors and FP32 accumulation.  Included by spmv.cu only.
+//
+// Design (GB300, sm_103a)
+// -----------------------
+// The rows are cut into tiles (fixed row blocks, or blocks balanced on
+// rows + entries).  A persistent grid of CTAs walks the tiles round-robin.
+// Each CTA has one producer warp and NT consumer threads:
+//
+//  * the producer stages, per tile, the row pointers, values and indices and
+//    the tile's x window -- the few contiguous x segments the tile's columns
+//    fall into, found at plan time -- into a ring of shared-memory stages with
+//    bulk asynchronous copies (cp.async.bulk, evict-first for the matrix)
+//    completing on an mbarrier;
+//  * the consumers compute the tile entirely from shared memory: DA-CSR reads
+//    x at row + off (the shifted view of Listing 2), CSR at col, through a
+//    branch-free map from the column to its slot in the staged window.  Tiles
+//    whose window does not fit a stage gather x from global memory instead.
+//
+// Staging x is what lets the FP64 FMAs overlap the matrix stream: on this part
+// a DFMA warp instruction occupies an SM sub-partition's FP64 unit for ~70
+// cycles whatever the active lanes, so the FMA chains must never wait for
+// ~1 us L2 gathers.
+//
+// Two compute modes keep FP64 FMA lanes dense:
+//
+//  mode 0 (one row per thread): thread i owns row i of the tile and runs the
+//    row's FMA chain in stored order.  Each warp loads its rows of tile j+1
+//    (values and x into registers, then hands the stage back) before running
+//    the FMAs of tile j; the warps do not wait for each other.  For rows of
+//    nearly equal length.
+//  mode 1 (balanced slices): the tile's m entries are cut into NT contiguous
+//    slices of ceil(m/NT); every thread runs exactly its slice's FMAs,
+//    writing finished rows to shared memory and the partial sum of a row that
+//    continues into the next slice to carry[i].  After a barrier, the thread
+//    that finishes a row begun in an earlier slice adds the carries of the
+//    slices the row spans, left to right.
+//
+// Summation order depends only on the tile partition and NT, so for one plan
+// CSR-32 and DA-CSR-16 give bitwise equal results.  Tiles whose entries do not
+// fit a stage are computed in the plan's mode from global memory.
+//
+// Every mbarrier wait is bounded (global timer); a wait that gives up records
+// DAMN_ERR_TIMEOUT in the library status word, and the CTA drains its own
+// copies (bounded) and returns.
+#pragma once
+
+#include <climits>
+
+#include "damn_common.cuh"
+
+namespace damn {
+namespace spmvk {
+
+constexpr int kXSegMax = 4;        // x segments per tile
+constexpr int kMaxStages = 8;
+
+// x window of one tile, computed at plan time: segments of x that start at
+// columns lo[i] (ascending, disjoint); nseg == 0: the tile gathers x from
+// global memory.  Segment i is bulk-copied from element src[i] (its 16-byte
+// aligned start) for cnt[i] elements to the shared slots starting at
+// pos[i] - (lo[i] - src[i]), so that column lo[i] lands at slot pos[i].
+// Windows that would need a partial 16-byte block at the end of x are not
+// staged.
+struct __align__(16) XSeg {
+  int nseg;
+  int pad[3];
+  int lo[kXSegMax];
+  int pos[kXSegMax];
+  int src[kXSegMax];
+  int cnt[kXSegMax];
+};
+
+struct TileHdr {
+  int r0, nr, k0, m, rp_sh, v_sh, i_sh, direct;
+  int nseg;
+  int xlo[kXSegMax];   // first column of segment i
+  int xpos[kXSegMax];  // shared-memory slot of column xlo[i]
+};
+
+struct SpmvParams {
+  int nrows, ncols;
+  long long nnz;
+  const int *rowptr;
+  const void *idx;
+  const void *val;
+  const void *x;
+  const void *y0;
+  void *y;
+  double alpha, beta;
+  int ab_mode;         // 0: y = acc, 1: y = alpha acc, 2: y = alpha acc + beta y0
+  int mode;            // 0 one row per thread, 1 balanced slices
+  int ntiles;
+  int rows_per_tile;   // > 0: fixed row tiles; 0: tile bounds from `bounds`
+  const int2 *bounds;  // {first row, rowptr[first row]} per tile, ntiles + 1 entries
+  const XSeg *xseg;    // per tile x window (NULL: gather everything)
+  const void *dot_w;
+  int dot_self;
+  double *dot_partials;
+  int stages;          // depth of the shared-memory ring (<= kMaxStages)
+  int *status;
+  unsigned long long timeout_ns;
+};
+
+template <int NT_, int CAP_NZ_, int CAP_ROWS_, int XBYTES_>
+struct KCfg {
+  static constexpr int NT = NT_, CAP_NZ = CAP_NZ_, CAP_ROWS = CAP_ROWS_, XBYTES = XBYTES_;
+};
+
+// 224 consumers (7 warps + producer = 8 warps: two CTAs per SM leave 128
+// registers per thread), stages of 1792 entries: rows of up to ~8 entries.
+// 128 consumers, stages of 3584 entries: rows of up to ~28 entries.
+using Cfg224 = KCfg<224, 1792, 512, 12288>;
+using Cfg128 = KCfg<128, 3584, 128, 12288>;
+
+constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Shared memory: [stage 0 .. stage S-1][control][mode-1 buffers]
+template <typename V, typename I, class C>
+struct Layout {
+  using A = typename AccOf<V>::type;
+  static constexpr int EV = 16 / (int)sizeof(V), EI = 16 / (int)sizeof(I), EX = 16 / (int)sizeof(A);
+  static constexpr int XCAP = C::XBYTES / (int)sizeof(A);  // staged x elements per tile
+  static constexpr size_t RP_BYTES = align_up((C::CAP_ROWS + 1 + 8) * 4, 128);
+  static constexpr size_t V_BYTES = align_up((C::CAP_NZ + 2 * EV) * sizeof(V), 128);
+  static constexpr size_t I_BYTES = align_up((C::CAP_NZ + 2 * EI) * sizeof(I), 128);
+  static constexpr size_t X_BYTES = align_up((XCAP + 2 * kXSegMax * EX) * sizeof(A), 128);
+  static constexpr size_t OFF_V = RP_BYTES, OFF_I = RP_BYTES + V_BYTES,
+                          OFF_X = RP_BYTES + V_BYTES + I_BYTES;
+  static constexpr size_t STAGE = OFF_X + X_BYTES;
+  static constexpr size_t C_FULL = 0;
+  static constexpr size_t C_EMPTY = kMaxStages * 8;
+  static constexpr size_t C_HDR = 2 * kMaxStages * 8;
+  static constexpr size_t C_RED = align_up(C_HDR + kMaxStages * sizeof(TileHdr), 16);
+  static constexpr size_t CTRL = align_up(C_RED + (C::NT / 32) * sizeof(double), 128);
+  static constexpr size_t M1_CARRY = 0;
+  static constexpr size_t M1_ROWSUM = 2 * C::NT * sizeof(A);
+  static constexpr size_t M1_BYTES = M1_ROWSUM + 2 * C::CAP_ROWS * sizeof(A);
+  static size_t total(int stages, int mode) {
+    return stages * STAGE + CTRL + (mode == 1 ? M1_BYTES : 0);
+  }
+};
+
+// Element range [first, first+count) of an array of len elements, split into a
+// 16-byte aligned bulk part [a0, b1) and a plainly loaded tail [tb, first+count)
+// beyond the array's last full 16-byte block.
+struct Range {
+  long long a0, tb;
+  uint32_t bulk_bytes;
+};
+
+template <int ESZ>
+__device__ __forceinline__ Range split_range(long long first, long long count, long long len) {
+  constexpr long long E = 16 / ESZ;
+  Range r;
+  r.a0 = first & ~(E - 1);
+  const long long a1 = (first + count + E - 1) & ~(E - 1);
+  const long long full_end = len & ~(E - 1);
+  const long long b1 = a1 < full_end ? a1 : full_end;
+  r.bulk_bytes = b1 > r.a0 ? static_cast<uint32_t>((b1 - r.a0) * ESZ) : 0u;
+  r.tb = b1 > r.a0 ? b1 : r.a0;
+  return r;
+}
+
+// ----------------------------------------------------------------------------
+// Producer
+// ----------------------------------------------------------------------------
+
+// What a producer lane prefetches for one tile.
+struct TileMeta {
+  int r0, r1, k0, k1, nseg;
+  int lo[kXSegMax], pos[kXSegMax], src[kXSegMax], cnt[kXSegMax];
+};
+
+template <class C>
+__device__ __forceinline__ void load_meta(const SpmvParams &p, long long t, TileMeta &mt) {
+  if (p.rows_per_tile > 0) {
+    mt.r0 = static_cast<int>(t * p.rows_per_tile);
+    mt.r1 = min(mt.r0 + p.rows_per_tile, p.nrows);
+    mt.k0 = __ldg(p.rowptr + mt.r0);
+    mt.k1 = __ldg(p.rowptr + mt.r1);
+  } else {
+    const int2 b0 = __ldg(p.bounds + t), b1 = __ldg(p.bounds + t + 1);
+    mt.r0 = b0.x; mt.k0 = b0.y; mt.r1 = b1.x; mt.k1 = b1.y;
+  }
+  mt.nseg = 0;
+  if (p.xseg && mt.k1 - mt.k0 <= C::CAP_NZ) {
+    const XSeg *xs = p.xseg + t;
+    mt.nseg = __ldg(&xs->nseg);
+    const int4 lo = __ldg(reinterpret_cast<const int4 *>(xs->lo));
+    const int4 pos = __ldg(reinterpret_cast<const int4 *>(xs->pos));
+    const int4 src = __ldg(reinterpret_cast<const int4 *>(xs->src));
+    const int4 cnt = __ldg(reinterpret_cast<const int4 *>(xs->cnt));
+    mt.lo[0] = lo.x; mt.lo[1] = lo.y; mt.lo[2] = lo.z; mt.lo[3] = lo.w;
+    mt.pos[0] = pos.x; mt.pos[1] = pos.y; mt.pos[2] = pos.z; mt.pos[3] = pos.w;
+    mt.src[0] = src.x; mt.src[1] = src.y; mt.src[2] = src.z; mt.src[3] = src.w;
+    mt.cnt[0] = cnt.x; mt.cnt[1] = cnt.y; mt.cnt[2] = cnt.z; mt.cnt[3] = cnt.w;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_tail(T *dst, const T *src, long long a0, long long tb,
+                                          long long end) {
+  for (long long e = tb; e < end; ++e) dst[e - a0] = src[e];
+}
+
+// Issues one tile into stage s (one lane).  Returns false when the wait for a
+// free stage gave up.
+template <typename V, typename I, class C>
+__device__ __forceinline__ bool issue_tile(const SpmvParams &p, unsigned char *smem, uint64_t *full,
+                                           uint64_t *empty, TileHdr *hdr, const TileMeta &mt,
+                                           int j, uint64_t pol) {
+  using L = Layout<V, I, C>;
+  using A = typename L::A;
+  const int S = p.stages;
+  const int s = j % S;
+  if (j >= S && !mbar_wait_bounded(&empty[s], ((j / S) - 1) & 1, p.status, p.timeout_ns))
+    return false;
+  unsigned char *st = smem + (size_t)s * L::STAGE;
+  int *rp_s = reinterpret_cast<int *>(st);
+  V *v_s = reinterpret_cast<V *>(st + L::OFF_V);
+  I *i_s = reinterpret_cast<I *>(st + L::OFF_I);
+  A *x_s = reinterpret_cast<A *>(st + L::OFF_X);
+  const V *val = static_cast<const V *>(p.val);
+  const I *idx = static_cast<const I *>(p.idx);
+  const A *x = static_cast<const A *>(p.x);
+  TileHdr &h = hdr[s];
+  const int nr = mt.r1 - mt.r0, m = mt.k1 - mt.k0;
+  const int direct = m > C::CAP_NZ ? 1 : 0;
+  const int nseg = direct ? 0 : mt.nseg;
+  const Range rr = split_range<4>(mt.r0, nr + 1, (long long)p.nrows + 1);
+  if (rr.tb < mt.r1 + 1) load_tail(rp_s, p.rowptr, rr.a0, rr.tb, (long long)mt.r1 + 1);
+  Range rv{mt.k0, mt.k0, 0u}, ri{mt.k0, mt.k0, 0u};
+  if (!direct && m > 0) {
+    rv = split_range<(int)sizeof(V)>(mt.k0, m, p.nnz);
+    ri = split_range<(int)sizeof(I)>(mt.k0, m, p.nnz);
+    if (rv.tb < mt.k1) load_tail(v_s, val, rv.a0, rv.tb, (long long)mt.k1);
+    if (ri.tb < mt.k1) load_tail(i_s, idx, ri.a0, ri.tb, (long long)mt.k1);
+  }
+  h.r0 = mt.r0; h.nr = nr; h.k0 = mt.k0; h.m = m; h.direct = direct; h.nseg = nseg;
+  h.rp_sh = static_cast<int>(mt.r0 - rr.a0);
+  h.v_sh = static_cast<int>(mt.k0 - rv.a0);
+  h.i_sh = static_cast<int>(mt.k0 - ri.a0);
+  uint32_t bytes = rr.bulk_bytes + rv.bulk_bytes + ri.bulk_bytes;
+#pragma unroll
+  for (int q = 0; q < kXSegMax; ++q) {
+    h.xlo[q] = mt.lo[q];
+    h.xpos[q] = mt.pos[q];
+    if (q < nseg) bytes += static_cast<uint32_t>(mt.cnt[q]) * sizeof(A);
+  }
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(&full[s], bytes);
+  if (rr.bulk_bytes) bulk_copy_g2s(rp_s, p.rowptr + rr.a0, rr.bulk_bytes, &full[s], pol);
+  if (rv.bulk_bytes) bulk_copy_g2s(v_s, val + rv.a0, rv.bulk_bytes, &full[s], pol);
+  if (ri.bulk_bytes) bulk_copy_g2s(i_s, idx + ri.a0, ri.bulk_bytes, &full[s], pol);
+#pragma unroll
+  for (int q = 0; q < kXSegMax; ++q)
+    if (q < nseg && mt.cnt[q] > 0)
+      bulk_copy_g2s_nohint(x_s + (mt.pos[q] - (mt.lo[q] - mt.src[q])), x + mt.src[q],
+                           static_cast<uint32_t>(mt.cnt[q]) * sizeof(A), &full[s]);
+  return true;
+}
+
+// Producer warp: for each group of 32 consecutive tiles of this CTA, lane i
+// loads the bounds and staging descriptors of tile i (one round of memory
+// latency per 32 tiles, all lanes in parallel); then lane i issues tile i,
+// in tile order.
+template <typename V, typename I, class C>
+__device__ __forceinline__ void produce(const SpmvParams &p, unsigned char *smem, uint64_t *full,
+                                        uint64_t *empty, TileHdr *hdr) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t pol = l2_policy_evict_first();
+  int j = 0;
+  bool stop = false;
+  while (!stop) {
+    const long long tl = (long long)blockIdx.x + (long long)(j + lane) * gridDim.x;
+    TileMeta mt;
+    if (tl < p.ntiles) load_meta<C>(p, tl, mt);
+    const int jl = j + lane;
+    for (int i = 0; i < 32; ++i) {
+      const long long t = (long long)blockIdx.x + (long long)j * gridDim.x;
+      if (t >= p.ntiles) { stop = true; break; }
+      int ok = 1;
+      if (lane == i) ok = issue_tile<V, I, C>(p, smem, full, empty, hdr, mt, jl, pol) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, i);
+      if (!ok) { stop = true; break; }
+      ++j;
+    }
+  }
+  // Do not leave copies in flight: wait (bounded) for the last issued stages.
+  const int S = p.stages;
+  if (lane == 0)
+    for (int q = (j > S ? j - S : 0); q < j; ++q)
+      mbar_wait_bounded(&full[q % S], (q / S) & 1, p.status, p.timeout_ns);
+}
+
+// ----------------------------------------------------------------------------
+// Consumers
+// ----------------------------------------------------------------------------
+
+// Column -> shared-memory slot of the staged x window: with the (at most four)
+// segments sorted by first column and d_i = xpos_i - xlo_i,
+//   slot(c) = c + d_0 + [c >= xlo_1] (d_1 - d_0) + [c >= xlo_2] (d_2 - d_1) + ...
+// Unused segments have xlo = INT_MAX, so there is no branch and no indexing by
+// a runtime segment number: three compares, selects and adds per entry.
+struct XMap {
+  int d0, lo1, lo2, lo3, dd1, dd2, dd3;
+  __device__ __forceinline__ void load(const TileHdr &h) {
+    const int n = h.nseg;
+    const int e0 = h.xpos[0] - h.xlo[0];
+    const int e1 = n > 1 ? h.xpos[1] - h.xlo[1] : e0;
+    const int e2 = n > 2 ? h.xpos[2] - h.xlo[2] : e1;
+    const int e3 = n > 3 ? h.xpos[3] - h.xlo[3] : e2;
+    d0 = e0;
+    lo1 = n > 1 ? h.xlo[1] : INT_MAX;
+    lo2 = n > 2 ? h.xlo[2] : INT_MAX;
+    lo3 = n > 3 ? h.xlo[3] : INT_MAX;
+    dd1 = e1 - e0;
+    dd2 = e2 - e1;
+    dd3 = e3 - e2;
+  }
+  __device__ __forceinline__ int slot(int c) const {
+    return c + d0 + (c >= lo1 ? dd1 : 0) + (c >= lo2 ? dd2 : 0) + (c >= lo3 ? dd3 : 0);
+  }
+};
+
+// y[row] <- alpha acc + beta y0[row] (+ optional fused dot).  PLAIN is the
+// common y = A x case: no floating-point operation in the epilogue.
+template <bool PLAIN, typename A>
+__device__ __forceinline__ void store_row(const SpmvParams &p, int row, A acc, double &dsum) {
+  if (PLAIN) {
+    static_cast<A *>(p.y)[row] = acc;
+    return;
+  }
+  A out;
+  if (p.ab_mode == 0) {
+    out = acc;
+  } else if (p.ab_mode == 1) {
+    out = static_cast<A>(p.alpha) * acc;
+  } else {
+    out = fma_acc(static_cast<A>(p.beta), static_cast<const A *>(p.y0)[row],
+                  static_cast<A>(p.alpha) * acc);
+  }
+  static_cast<A *>(p.y)[row] = out;
+  if (p.dot_w)
+    dsum = __fma_rn(static_cast<double>(static_cast<const A *>(p.dot_w)[row]),
+                    static_cast<double>(out), dsum);
+  else if (p.dot_self)
+    dsum = __fma_rn(static_cast<double>(out), static_cast<double>(out), dsum);
+}
+
+// Pointers of a tile's values / indices / staged x (element 0 = entry k0).
+template <typename V, typename I, class C>
+struct TileView {
+  using A = typename AccOf<V>::type;
+  const int *rp;  // rp[lr] = rowptr[r0 + lr]
+  const V *vs;
+  const I *is;
+  const A *xs;    // staged x window (valid when nseg > 0)
+  __device__ __forceinline__ void init(const SpmvParams &p, unsigned char *smem, const TileHdr &h,
+                                       int s) {
+    using L = Layout<V, I, C>;
+    unsigned char *st = smem + (size_t)s * L::STAGE;
+    rp = reinterpret_cast<const int *>(st) + h.rp_sh;
+    vs = h.direct ? static_cast<const V *>(p.val) + h.k0 : reinterpret_cast<const V *>(st + L::OFF_V) + h.v_sh;
+    is = h.direct ? static_cast<const I *>(p.idx) + h.k0 : reinterpret_cast<const I *>(st + L::OFF_I) + h.i_sh;
+    xs = reinterpret_cast<const A *>(st + L::OFF_X);
+  }
+};
+
+// x value of column c: from the staged window or gathered from global memory.
+template <typename A>
+__device__ __forceinline__ A x_at(const A *xg, const A *xs, const XMap &xm, bool staged, int c) {
+  return staged ? xs[xm.slot(c)] : ldg(xg + c);
+}
+
+// Mode 0 -------------------------------------------------------------------
+template <typename V, typename I>
+struct RowWork {
+  using A = typename AccOf<V>::type;
+  static constexpr int U = 8;
+  A av[U], xv[U];
+  int row, cnt;      // row (-1: none); number of entries of the row
+  int s;             // stage the tile came from
+  bool released;     // stage already handed back to the producer
+};
+
+template <typename V, typename I, class C>
+__device__ __forceinline__ bool fetch_rows(const SpmvParams &p, unsigned char *smem,
+                                           uint64_t *full, uint64_t *empty, const TileHdr *hdr,
+                                           int j, int ctid, RowWork<V, I> &w) {
+  using A = typename AccOf<V>::type;
+  constexpr bool DA = sizeof(I) == 2;
+  constexpr int U = RowWork<V, I>::U;
+  const int s = j % p.stages;
+  if (!mbar_wait_bounded(&full[s], (j / p.stages) & 1, p.status, p.timeout_ns)) return false;
+  const TileHdr &h = hdr[s];
+  const int nr = h.nr, k0 = h.k0, r0 = h.r0;
+  const bool direct = h.direct != 0;
+  const bool staged = h.nseg > 0;
+  TileView<V, I, C> tv;
+  tv.init(p, smem, h, s);
+  XMap xm;
+  if (staged) xm.load(h);
+  const A *xg = static_cast<const A *>(p.x);
+  w.s = s;
+  w.row = -1;
+  w.cnt = 0;
+  if (ctid < nr) {
+    w.row = r0 + ctid;
+    const int b = tv.rp[ctid] - k0;
+    w.cnt = tv.rp[ctid + 1] - k0 - b;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (u < w.cnt) {
+        const int c = static_cast<int>(tv.is[b + u]) + (DA ? w.row : 0);
+        w.av[u] = to_acc(tv.vs[b + u]);
+        w.xv[u] = x_at(xg, tv.xs, xm, staged, c);
+      }
+    }
+  }
+  // Every row of this warp now in registers: hand the stage back at once (the
+  // arrive orders the shared-memory reads above before it).
+  w.released = false;
+  if (!direct && nr <= C::NT && __all_sync(0xffffffffu, w.cnt <= U)) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);
+    w.released = true;
+  }
+  return true;
+}
+
+template <bool PLAIN, typename V, typename I, class C>
+__device__ __forceinline__ void finish_rows(const SpmvParams &p, unsigned char *smem,
+                                            uint64_t *empty, const TileHdr *hdr, int ctid,
+                                            RowWork<V, I> &w, double &dsum) {
+  using A = typename AccOf<V>::type;
+  constexpr bool DA = sizeof(I) == 2;
+  constexpr int U = RowWork<V, I>::U;
+  if (w.row >= 0) {
+    A acc = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (u < w.cnt) acc = fma_acc(w.av[u], w.xv[u], acc);
+    if (w.cnt > U) {  // long row: the stage is still held, finish from it
+      const TileHdr &h = hdr[w.s];
+      TileView<V, I, C> tv;
+      tv.init(p, smem, h, w.s);
+      XMap xm;
+      const bool staged = h.nseg > 0;
+      if (staged) xm.load(h);
+      const A *xg = static_cast<const A *>(p.x);
+      const int b = tv.rp[ctid] - h.k0;
+      for (int q = b + U; q < b + w.cnt; ++q)
+        acc = fma_acc(to_acc(tv.vs[q]),
+                      x_at(xg, tv.xs, xm, staged, static_cast<int>(tv.is[q]) + (DA ? w.row : 0)),
+                      acc);
+    }
+    store_row<PLAIN>(p, w.row, acc, dsum);
+  }
+  if (!w.released) {
+    const TileHdr &h = hdr[w.s];
+    if (h.nr > C::NT) {  // rows beyond the first NT (not produced by mode-0 plans)
+      TileView<V, I, C> tv;
+      tv.init(p, smem, h, w.s);
+      XMap xm;
+      const bool staged = h.nseg > 0;
+      if (staged) xm.load(h);
+      const A *xg = static_cast<const A *>(p.x);
+      for (int lr = ctid + C::NT; lr < h.nr; lr += C::NT) {
+        const int row = h.r0 + lr;
+        A acc = 0;
+        for (int q = tv.rp[lr] - h.k0; q < tv.rp[lr + 1] - h.k0; ++q)
+          acc = fma_acc(to_acc(tv.vs[q]),
+                        x_at(xg, tv.xs, xm, staged, static_cast<int>(tv.is[q]) + (DA ? row : 0)),
+                        acc);
+        store_row<PLAIN>(p, row, acc, dsum);
+      }
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[w.s]);
+  }
+}
+
+template <bool PLAIN, typename V, typename I, class C>
+__device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char *smem,
+                                             uint64_t *full, uint64_t *empty, const TileHdr *hdr,
+                                             int ctid, double &dsum) {
+  // While the FMAs of tile j run, tile j+1 is already loaded into the other
+  // register set (warps do not wait for each other).
+  RowWork<V, I> w0, w1;
+  auto has = [&](int jj) {
+    return (long long)blockIdx.x + (long long)jj * gridDim.x < p.ntiles;
+  };
+  int j = 0;
+  if (!has(0) || !fetch_rows<V, I, C>(p, smem, full, empty, hdr, 0, ctid, w0)) return;
+  while (true) {
+    const bool v1 = has(j + 1) && fetch_rows<V, I, C>(p, smem, full, empty, hdr, j + 1, ctid, w1);
+    finish_rows<PLAIN, V, I, C>(p, smem, empty, hdr, ctid, w0, dsum);
+    if (!v1) return;
+    ++j;
+    const bool v0 = has(j + 1) && fetch_rows<V, I, C>(p, smem, full, empty, hdr, j + 1, ctid, w0);
+    finish_rows<PLAIN, V, I, C>(p, smem, empty, hdr, ctid, w1, dsum);
+    if (!v0) return;
+    ++j;
+  }
+}
+
+// Mode 1 -------------------------------------------------------------------
+template <bool PLAIN, typename V, typename I, class C>
+__device__ __forceinline__ void tile_slices(const SpmvParams &p, const TileHdr &h,
+                                            const TileView<V, I, C> &tv, int ctid,
+                                            typename AccOf<V>::type *carry,
+                                            typename AccOf<V>::type *rowsum, double &dsum) {
+  using A = typename AccOf<V>::type;
+  constexpr bool DA = sizeof(I) == 2;
+  constexpr int G = 8;
+  const A *xg = static_cast<const A *>(p.x);
+  const int *rp = tv.rp;
+  const int nr = h.nr, m = h.m, k0 = h.k0;
+  const bool staged = h.nseg > 0;
+  XMap xm;
+  if (staged) xm.load(h);
+  const int K = m > 0 ? (m + C::NT - 1) / C::NT : 0;
+  const int s = ctid * K;
+  const int e = min(s + K, m);
+  const bool has = s < m;
+  const int last = m > 0 ? (m - 1) / K : 0;
+  int pend_row = -1;
+  A pend_acc = 0;
+  if (has || ctid == last) {
+    int lo = 0, hi = nr;  // first row whose start is >= s
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (rp[mid] - k0 >= s) hi = mid; else lo = mid + 1;
+    }
+    bool cont = (s > 0) && (lo == nr || rp[lo] - k0 > s);
+    int cr = cont ? lo - 1 : lo;
+    int cend = (cr < nr) ? rp[cr + 1] - k0 : m;
+    A acc = 0;
+    for (int q = s; q < e; q += G) {
+      A av[G], xv[G];
+      int tcr = cr, tend = cend;
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        if (q + u < e) {
+          while (tend <= q + u) { ++tcr; tend = rp[tcr + 1] - k0; }
+          const int c = static_cast<int>(tv.is[q + u]) + (DA ? h.r0 + tcr : 0);
+          av[u] = to_acc(tv.vs[q + u]);
+          xv[u] = x_at(xg, tv.xs, xm, staged, c);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        if (q + u < e) {
+          while (cend <= q + u) {
+            if (cont) { pend_row = cr; pend_acc = acc; } else { rowsum[cr] = acc; }
+            acc = 0; cont = false; ++cr; cend = rp[cr + 1] - k0;
+          }
+          acc = fma_acc(av[u], xv[u], acc);
+        }
+      }
+    }
+    if (has) {
+      if (cend == e) {
+        if (cont) { pend_row = cr; pend_acc = acc; } else { rowsum[cr] = acc; }
+        ++cr;
+        if (e == m)
+          for (; cr < nr; ++cr) rowsum[cr] = 0;  // empty rows at the tile end
+      } else {
+        carry[ctid] = acc;
+      }
+    } else {
+      for (int r = 0; r < nr; ++r) rowsum[r] = 0;  // tile without entries
+    }
+  }
+  named_bar_sync(1, C::NT);
+  if (pend_row >= 0) {
+    const int a = (rp[pend_row] - k0) / K;
+    A tot = carry[a];
+    for (int jj = a + 1; jj < ctid; ++jj) tot += carry[jj];
+    rowsum[pend_row] = tot + pend_acc;
+  }
+  named_bar_sync(1, C::NT);
+  for (int lr = ctid; lr < nr; lr += C::NT) store_row<PLAIN>(p, h.r0 + lr, rowsum[lr], dsum);
+}
+
+// ----------------------------------------------------------------------------
+// Kernel
+// ----------------------------------------------------------------------------
+template <bool PLAIN, typename V, typename I, class C>
+__global__ void __launch_bounds__(C::NT + 32, 2) k_spmv(const SpmvParams p) {
+  using A = typename AccOf<V>::type;
+  using L = Layout<V, I, C>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char *ctrl = smem + (size_t)p.stages * L::STAGE;
+  uint64_t *full = reinterpret_cast<uint64_t *>(ctrl + L::C_FULL);
+  uint64_t *empty = reinterpret_cast<uint64_t *>(ctrl + L::C_EMPTY);
+  TileHdr *hdr = reinterpret_cast<TileHdr *>(ctrl + L::C_HDR);
+  double *red = reinterpret_cast<double *>(ctrl + L::C_RED);
+  A *carry = reinterpret_cast<A *>(ctrl + L::CTRL + L::M1_CARRY);
+  A *rowsum = reinterpret_cast<A *>(ctrl + L::CTRL + L::M1_ROWSUM);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], C::NT / 32);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid < 32) {
+    produce<V, I, C>(p, smem, full, empty, hdr);
+    return;
+  }
+  const int ctid = tid - 32;
+  double dsum = 0.0;
+  if (p.mode == 0) {
+    consume_rows<PLAIN, V, I, C>(p, smem, full, empty, hdr, ctid, dsum);
+  } else {
+    int j = 0;
+    for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++j) {
+      const int s = j % p.stages;
+      const bool got = mbar_wait_bounded(&full[s], (j / p.stages) & 1, p.status, p.timeout_ns);
+      // the consumers synchronise inside a tile, so they give up together
+      if (named_bar_or(2, C::NT, !got)) break;
+      const TileHdr &h = hdr[s];
+      TileView<V, I, C> tv;
+      tv.init(p, smem, h, s);
+      tile_slices<PLAIN, V, I, C>(p, h, tv, ctid, carry + (j & 1) * C::NT,
+                                  rowsum + (j & 1) * C::CAP_ROWS, dsum);
+      __syncwarp();
+      if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+    }
+  }
+  if (p.dot_partials) {
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    if ((ctid & 31) == 0) red[ctid >> 5] = dsum;
+    named_bar_sync(3, C::NT);
+    if (ctid == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < C::NT / 32; ++w) tot += red[w];
+      p.dot_partials[blockIdx.x] = tot;
+    }
+  }
+}
+
+}  // namespace spmvk
+}  // namespace damn

@@ -1,0 +1,324 @@
+"""Thin Python binding of the DA-CSR CUDA library (``include/damn.h``).
+
+Argument marshalling only: every function takes torch tensors that live on
+the current CUDA device, passes their device pointers and the current CUDA
+stream to the C entry point of the same name, and raises ``DamnError`` on a
+non-zero status.  All arithmetic runs in the library's kernels; there is no
+CPU fallback, and importing this module fails loudly when the compiled library
+is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libdamn.so")
+
+DAMN_OK = 0
+DAMN_ERR_INVALID_ARG = -1
+DAMN_ERR_NOFIT = -2
+DAMN_ERR_CUDA = -3
+DAMN_ERR_NOT_CONVERGED = -4
+DAMN_ERR_TIMEOUT = -5
+DAMN_ERR_UNSUPPORTED = -6
+
+DAMN_F64, DAMN_F32, DAMN_BF16 = 0, 1, 2
+DAMN_FMT_CSR32, DAMN_FMT_DACSR16 = 0, 1
+DAMN_TILING_SLICES, DAMN_TILING_ROWS, DAMN_TILING_ROWS_LONG = 0, 1, 2
+
+_DTYPE_CODE = {torch.float64: DAMN_F64, torch.float32: DAMN_F32, torch.bfloat16: DAMN_BF16}
+_VEC_DTYPE = {DAMN_F64: torch.float64, DAMN_F32: torch.float32, DAMN_BF16: torch.float32}
+
+
+class DamnError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"DA-CSR CUDA library not built: {LIB_PATH} is missing "
+                      "(run paper_2307_06305_gb300/build.py or __graft_entry__.build())")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+F64 = ctypes.c_double
+SZ = ctypes.c_size_t
+
+
+class damn_fit_info(ctypes.Structure):
+    _fields_ = [("min_off", I32), ("max_off", I32), ("w", I64), ("n_fit", I64), ("n_bad", I64),
+                ("fits", I32), ("reserved", I32)]
+
+
+class damn_bw_info(ctypes.Structure):
+    _fields_ = [("w_before", I64), ("w_after", I64)]
+
+
+class damn_plan_desc(ctypes.Structure):
+    _fields_ = [("mode", I32), ("tile_items", I32), ("ntiles", I32), ("grid", I32),
+                ("stages", I32), ("threads", I32), ("row_efficiency", F64), ("max_row", I32),
+                ("dtype", I32), ("tiling", I32), ("x_staged_tiles", I32)]
+
+
+class damn_cg_result(ctypes.Structure):
+    _fields_ = [("iterations", I32), ("outer", I32), ("converged", I32), ("reserved", I32),
+                ("relres", F64), ("true_relres", F64)]
+
+
+class damn_mat_desc(ctypes.Structure):
+    _fields_ = [("nrows", I32), ("ncols", I32), ("nnz", I64), ("rowptr", P), ("off", P),
+                ("val", P), ("X", P), ("Y", P)]
+
+
+class damn_batch_desc(ctypes.Structure):
+    _fields_ = [("count", I32), ("k", I32), ("dtype", I32), ("ntiles", I32), ("grid", I32),
+                ("threads", I32), ("tile_items", I32), ("graph_ready", I32), ("tune_ms", F64)]
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("damn_last_error", ctypes.c_char_p, [])
+_sig("damn_version", ctypes.c_int, [])
+_sig("damn_device_status", ctypes.c_int, [ctypes.POINTER(I32), ctypes.c_int, P])
+_sig("damn_selftest_wait_timeout", ctypes.c_int, [I64, P])
+_sig("damn_csr_to_dacsr_workspace_size", SZ, [])
+_sig("damn_csr_to_dacsr", ctypes.c_int,
+     [I32, I32, I64, P, P, P, ctypes.POINTER(damn_fit_info), P, SZ, P])
+_sig("damn_validate_csr_workspace_size", SZ, [])
+_sig("damn_validate_csr", ctypes.c_int,
+     [I32, I32, I64, P, P, ctypes.POINTER(I64), ctypes.POINTER(I64), P, SZ, P])
+_sig("damn_cast_values", ctypes.c_int, [I64, P, ctypes.c_int, P, ctypes.c_int, P])
+_sig("damn_plan_create", ctypes.c_int,
+     [I32, I32, I64, P, ctypes.c_int, P, ctypes.c_int, P, ctypes.POINTER(P)])
+_sig("damn_plan_autotune", ctypes.c_int, [P, ctypes.c_int, P, P, P, P, P])
+_sig("damn_plan_describe", ctypes.c_int, [P, ctypes.POINTER(damn_plan_desc)])
+_sig("damn_plan_set_tiling", ctypes.c_int, [P, ctypes.c_int])
+_sig("damn_plan_destroy", ctypes.c_int, [P])
+_sig("damn_spmv_csr32", ctypes.c_int,
+     [I32, I32, I64, P, P, P, ctypes.c_int, P, P, F64, F64, P, P])
+_sig("damn_spmv_dacsr16", ctypes.c_int,
+     [I32, I32, I64, P, P, P, ctypes.c_int, P, P, F64, F64, P, P])
+
+_OPTIONAL = {}
+
+
+def _opt(name, res, args):
+    try:
+        _OPTIONAL[name] = _sig(name, res, args)
+    except AttributeError:
+        pass
+
+
+_opt("damn_rcm_order", ctypes.c_int, [I32, I64, P, P, P, ctypes.POINTER(I64), ctypes.POINTER(I64)])
+_opt("damn_permute_sym_workspace_size", SZ, [I32])
+_opt("damn_permute_sym", ctypes.c_int, [I32, I64, P, P, P, ctypes.c_int, P, P, P, P, P, SZ, P])
+_opt("damn_rcm_permute", ctypes.c_int,
+     [I32, I64, P, P, P, ctypes.c_int, P, P, P, P, ctypes.POINTER(damn_bw_info), P, SZ, P])
+_opt("damn_cg_workspace_size", SZ, [I32])
+_opt("damn_cg", ctypes.c_int,
+     [I32, I64, P, P, P, P, P, F64, I32, P, ctypes.POINTER(damn_cg_result), P, SZ, P])
+_opt("damn_cg_ir_workspace_size", SZ, [I32])
+_opt("damn_cg_ir", ctypes.c_int,
+     [I32, I64, P, P, P, P, ctypes.c_int, P, P, F64, F64, I32, I32, P, P,
+      ctypes.POINTER(damn_cg_result), P, SZ, P])
+_opt("damn_spmm_dacsr16", ctypes.c_int, [I32, I32, I64, P, P, P, ctypes.c_int, I32, P, P, P])
+_opt("damn_batch_plan_create", ctypes.c_int,
+     [I32, ctypes.POINTER(damn_mat_desc), I32, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(P)])
+_opt("damn_batch_plan_describe", ctypes.c_int, [P, ctypes.POINTER(damn_batch_desc)])
+_opt("damn_batch_plan_destroy", ctypes.c_int, [P])
+_opt("damn_spmm_dacsr16_batched", ctypes.c_int, [P, P])
+_opt("damn_batch_graph_launch", ctypes.c_int, [P, P])
+
+
+def _fn(name):
+    if name in _OPTIONAL:
+        return _OPTIONAL[name]
+    return getattr(_lib, name)
+
+
+def last_error() -> str:
+    return _lib.damn_last_error().decode(errors="replace")
+
+
+def _check(rc: int, what: str, allow=()):
+    if rc != DAMN_OK and rc not in allow:
+        raise DamnError(rc, f"{what}: {last_error()}")
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
+
+
+def damn_version() -> int:
+    return int(_lib.damn_version())
+
+
+def loaded_library_path() -> str:
+    return LIB_PATH
+
+
+# ----------------------------------------------------------------------------
+# diagnostics
+# ----------------------------------------------------------------------------
+
+def damn_device_status(reset: bool = False, stream=None) -> int:
+    v = I32(0)
+    _check(_lib.damn_device_status(ctypes.byref(v), int(reset), _stream(stream)), "damn_device_status")
+    return int(v.value)
+
+
+def damn_selftest_wait_timeout(timeout_ns: int, stream=None) -> int:
+    """Returns the library status (DAMN_ERR_TIMEOUT when the bounded wait gave up)."""
+    return int(_lib.damn_selftest_wait_timeout(int(timeout_ns), _stream(stream)))
+
+
+# ----------------------------------------------------------------------------
+# a1: conversion and fit check
+# ----------------------------------------------------------------------------
+
+@dataclass
+class FitInfo:
+    min_off: int
+    max_off: int
+    w: int
+    n_fit: int
+    n_bad: int
+    fits: bool
+
+
+def damn_csr_to_dacsr(rowptr: torch.Tensor, col: torch.Tensor, ncols: int, off_out=None,
+                      stream=None, raise_on_nofit: bool = False):
+    """Returns (off int16 tensor, FitInfo).  off is unspecified when not fits."""
+    nrows = rowptr.numel() - 1
+    nnz = col.numel()
+    if off_out is None:
+        off_out = torch.empty(nnz, dtype=torch.int16, device=col.device)
+    ws = _workspace(_lib.damn_csr_to_dacsr_workspace_size(), col.device)
+    info = damn_fit_info()
+    rc = _lib.damn_csr_to_dacsr(nrows, int(ncols), nnz, _ptr(rowptr), _ptr(col), _ptr(off_out),
+                                ctypes.byref(info), _ptr(ws), ws.numel(), _stream(stream))
+    _check(rc, "damn_csr_to_dacsr", allow=() if raise_on_nofit else (DAMN_ERR_NOFIT,))
+    return off_out, FitInfo(info.min_off, info.max_off, info.w, info.n_fit, info.n_bad,
+                            bool(info.fits))
+
+
+def damn_validate_csr(rowptr, col, ncols: int, stream=None):
+    nrows = rowptr.numel() - 1
+    ws = _workspace(_lib.damn_validate_csr_workspace_size(), rowptr.device)
+    br, bc = I64(0), I64(0)
+    rc = _lib.damn_validate_csr(nrows, int(ncols), col.numel(), _ptr(rowptr), _ptr(col),
+                                ctypes.byref(br), ctypes.byref(bc), _ptr(ws), ws.numel(),
+                                _stream(stream))
+    _check(rc, "damn_validate_csr", allow=(DAMN_ERR_INVALID_ARG,))
+    return int(br.value), int(bc.value)
+
+
+def damn_cast_values(src: torch.Tensor, dst_dtype: torch.dtype, stream=None) -> torch.Tensor:
+    dst = torch.empty(src.numel(), dtype=dst_dtype, device=src.device)
+    rc = _lib.damn_cast_values(src.numel(), _ptr(src), _DTYPE_CODE[src.dtype], _ptr(dst),
+                               _DTYPE_CODE[dst_dtype], _stream(stream))
+    _check(rc, "damn_cast_values")
+    return dst
+
+
+# ----------------------------------------------------------------------------
+# SpMV and plans
+# ----------------------------------------------------------------------------
+
+class Plan:
+    """Owns a damn_plan (tiling, compute mode, x windows) for one matrix and
+    one value dtype.  ``idx`` is the column array (int32 col for CSR-32 or
+    int16 off for DA-CSR-16; None: no x windows).  Keep rowptr and idx alive
+    while the plan is used."""
+
+    def __init__(self, rowptr: torch.Tensor, nnz: int, ncols: int, dtype: torch.dtype, idx=None,
+                 stream=None):
+        self.handle = P()
+        self.rowptr = rowptr
+        self.idx = idx
+        self.dtype_code = _DTYPE_CODE[dtype]
+        fmt = DAMN_FMT_DACSR16 if (idx is not None and idx.dtype == torch.int16) else DAMN_FMT_CSR32
+        rc = _lib.damn_plan_create(rowptr.numel() - 1, int(ncols), int(nnz), _ptr(rowptr), fmt,
+                                   _ptr(idx), self.dtype_code, _stream(stream),
+                                   ctypes.byref(self.handle))
+        _check(rc, "damn_plan_create")
+
+    def autotune(self, fmt: int, idx, val, x, y, stream=None):
+        rc = _lib.damn_plan_autotune(self.handle, int(fmt), _ptr(idx), _ptr(val), _ptr(x), _ptr(y),
+                                     _stream(stream))
+        _check(rc, "damn_plan_autotune")
+        return self
+
+    def set_tiling(self, tiling: int):
+        _check(_lib.damn_plan_set_tiling(self.handle, int(tiling)), "damn_plan_set_tiling")
+        return self
+
+    def describe(self) -> dict:
+        d = damn_plan_desc()
+        _check(_lib.damn_plan_describe(self.handle, ctypes.byref(d)), "damn_plan_describe")
+        return {k: getattr(d, k) for k, _ in damn_plan_desc._fields_}
+
+    def close(self):
+        if self.handle:
+            _lib.damn_plan_destroy(self.handle)
+            self.handle = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def damn_plan_create(rowptr, nnz, ncols, dtype, idx=None, stream=None) -> Plan:
+    return Plan(rowptr, nnz, ncols, dtype, idx, stream)
+
+
+def _plan_handle(plan):
+    return None if plan is None else plan.handle
+
+
+def damn_spmv_csr32(rowptr, col, val, x, y, alpha=1.0, beta=0.0, plan=None, ncols=None, stream=None):
+    nrows = rowptr.numel() - 1
+    ncols = x.numel() if ncols is None else ncols
+    rc = _lib.damn_spmv_csr32(nrows, int(ncols), col.numel(), _ptr(rowptr), _ptr(col), _ptr(val),
+                              _DTYPE_CODE[val.dtype], _ptr(x), _ptr(y), float(alpha), float(beta),
+                              _plan_handle(plan), _stream(stream))
+    _check(rc, "damn_spmv_csr32")
+    return y
+
+
+def damn_spmv_dacsr16(rowptr, off, val, x, y, alpha=1.0, beta=0.0, plan=None, ncols=None,
+                      stream=None):
+    nrows = rowptr.numel() - 1
+    ncols = x.numel() if ncols is None else ncols
+    rc = _lib.damn_spmv_dacsr16(nrows, int(ncols), off.numel(), _ptr(rowptr), _ptr(off), _ptr(val),
+                                _DTYPE_CODE[val.dtype], _ptr(x), _ptr(y), float(alpha),
+                                float(beta), _plan_handle(plan), _stream(stream))
+    _check(rc, "damn_spmv_dacsr16")
+    return y

@@ -46,3 +46,20 @@ def golden():
 @pytest.fixture
 def golden_rows():
     return read_golden_rows
+
+
+@pytest.fixture(scope="session")
+def cuda_dev():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="session")
+def D(cuda_dev):
+    """The DA-CSR binding (built in-tree)."""
+    from paper_2307_06305_gb300 import build as B
+    B.build()
+    from paper_2307_06305_gb300 import damn
+    return damn

@@ -1,0 +1,101 @@
+"""GPU parity of the CSR -> DA-CSR-16 translation and fit check (Section 2,
+Example 1) against the oracle: bit-exact offsets and fit information."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import dacsr as OD
+from oracle import spmv as OS
+
+pytestmark = pytest.mark.gpu
+
+
+def _to(dev, *arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in arrs]
+
+
+def _check(D, dev, n_rows, n_cols, rp, col):
+    t_rp, t_col = _to(dev, rp, col)
+    off, info = D.damn_csr_to_dacsr(t_rp, t_col, n_cols)
+    ref = OD.fit_check(n_rows, n_cols, rp, col)
+    assert (info.min_off, info.max_off, info.w, info.n_fit, info.n_bad, info.fits) == \
+        (ref.min_off, ref.max_off, ref.w, ref.n_fit, ref.n_bad, ref.fits)
+    if ref.fits:
+        assert np.array_equal(off.cpu().numpy(), OD.translate(n_rows, rp, col).astype(np.int16))
+    return info
+
+
+def test_example1(D, cuda_dev, golden):
+    g = golden("example1_dacsr.txt")
+    rp = np.array(g["rowptr"], dtype=np.int32)
+    col = np.array(g["colids_csr"], dtype=np.int32)
+    info = _check(D, cuda_dev, 4, 4, rp, col)
+    t_rp, t_col = _to(cuda_dev, rp, col)
+    off, _ = D.damn_csr_to_dacsr(t_rp, t_col, 4)
+    assert off.cpu().tolist() == [int(v) for v in g["colids_dacsr"]]
+    assert info.w == 1
+
+
+@pytest.mark.parametrize("n,h,seed", [(1, 1, 0), (511, 3, 1), (513, 40, 2), (5000, 100, 3),
+                                      (40000, 1000, 4), (100003, 30000, 5)])
+def test_random_banded(D, cuda_dev, n, h, seed):
+    rp, col, _ = W.random_banded(n, h, np.random.default_rng(seed))
+    _check(D, cuda_dev, n, n, rp, col)
+
+
+@pytest.mark.parametrize("extreme", [32767, -32768, 32768, -32769, 100000])
+def test_fit_boundary(D, cuda_dev, extreme):
+    n = 140000
+    r = 70000
+    rows = np.append(np.arange(n), r)
+    cols = np.append(np.arange(n), r + extreme)
+    rp, col, _ = W.from_coo(n, rows, cols)
+    info = _check(D, cuda_dev, n, n, rp, col)
+    assert info.fits == (-32768 <= extreme <= 32767)
+
+
+def test_empty_rows_nonsquare_and_bad_columns(D, cuda_dev):
+    rp = np.zeros(10, dtype=np.int32)
+    _check(D, cuda_dev, 9, 5, rp, np.zeros(0, dtype=np.int32))
+    rp, col, _ = W.from_coo(700, [0, 3, 5, 5, 699], [0, 1, 0, 2, 2])
+    _check(D, cuda_dev, 700, 3, rp, col)
+    info = _check(D, cuda_dev, 700, 2, rp, col)      # column 2 out of range
+    assert info.n_bad == 2 and not info.fits
+
+
+def test_laplace3d_full_size_and_scrambled(D, cuda_dev):
+    m = 128
+    rp, col, _ = W.laplace3d_7pt(m)
+    info = _check(D, cuda_dev, m ** 3, m ** 3, rp, col)
+    assert info.fits and info.w == m * m
+    rp2, col2, _ = W.laplace3d_7pt(m, scrambled=True, rng=W.rng_for(2, 1))
+    info2 = _check(D, cuda_dev, m ** 3, m ** 3, rp2, col2)
+    assert not info2.fits
+    rate = info2.n_fit / len(col2)
+    assert 0.15 < rate < 0.20     # diagonal (1/7) plus ~3% of the off-diagonals
+
+
+def test_validate_csr(D, cuda_dev):
+    rp, col, _ = W.random_banded(3000, 50, np.random.default_rng(9))
+    t_rp, t_col = _to(cuda_dev, rp, col)
+    assert D.damn_validate_csr(t_rp, t_col, 3000) == (0, 0)
+    bad_rp = rp.copy()
+    bad_rp[10] = bad_rp[11] + 1
+    bad_col = col.copy()
+    bad_col[[5, 7]] = [-1, 3000]
+    t_rp, t_col = _to(cuda_dev, bad_rp, bad_col)
+    br, bc = D.damn_validate_csr(t_rp, t_col, 3000)
+    assert br >= 1 and bc == 2
+
+
+def test_cast_values(D, cuda_dev):
+    rng = np.random.default_rng(4)
+    v = np.concatenate([rng.standard_normal(100000) * 10.0 ** rng.integers(-40, 40, 100000),
+                        [1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 2 ** -8 + 2 ** -40, 2.0 ** -133,
+                         2.0 ** -135, 3.4e38, -3.4e38, 0.0, -0.0, 26.5, -1.0]])
+    t = torch.from_numpy(v).to(cuda_dev)
+    f32 = D.damn_cast_values(t, torch.float32).double().cpu().numpy()
+    assert np.array_equal(f32, OS.quantize(v, "f32"))
+    bf = D.damn_cast_values(t, torch.bfloat16).double().cpu().numpy()
+    assert np.array_equal(bf, OS.quantize(v, "bf16"))
