@@ -1,0 +1,357 @@
+"""Benchmark: DA-CSR-16 vs CSR-32 SpMV throughput on GB300.
+
+Workload (the configuration the headline metric is quoted on): the 3-D
+7-point Laplacian on a 128^3 grid in natural order (n = 2,097,152 rows,
+nnz = 14,581,760, half-bandwidth 16,384), FP64 values, x ~ U[-1, 1).
+One step = one DA-CSR-16 SpMV y = A x through the C ABI.  Inputs are
+resident in HBM; consecutive steps cycle through 4 copies of the matrix
+(4 x 188 MB, larger than the 126 MB L2), so every step streams its matrix
+from HBM.  Throughput = algorithmic bytes (Section 4: the three arrays of
+Eq. (3), x read once, y written once) / time.
+
+Also reported in the same run: CSR-32 on the same matrix and plan (and the
+DA/CSR ratio), FP32 / BF16 value variants, an end-to-end number through the
+public API with host buffers (x uploaded and y downloaded every step), the
+roofline of the SpMV kernel against the measured HBM copy bandwidth, GPU
+clocks sampled during the timed region, and the plain-C oracle (Listing 2)
+timed on the host cores as a CPU baseline.
+
+``--impl reference`` times the oracle (the plain-C Listing 2 restatement)
+on the host cores instead, for the same metric and workload.
+
+Multi-GPU (torchrun): every rank runs its own copy of the workload (weak
+scaling, no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "DA-CSR16 vs CSR32 SpMV GB/s, % HBM peak; mixed-prec CG time-to-1e-10"
+WORKLOAD = "laplace3d_7pt_128^3_natural_dacsr16_f64_spmv"
+GRID = 128
+NCOPY = 4
+
+
+def spmv_bytes(n, nnz, idx_bytes, val_bytes, vec_bytes):
+    """Section 4 traffic: Eq. (3) with 32-bit row pointers, plus x read once
+    and y written once (beta = 0)."""
+    return (n + 1) * 4 + nnz * (idx_bytes + val_bytes) + 2 * n * vec_bytes
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("spmv_kernel.cuh", "spmv.cu", "damn_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2307_06305_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch from the committed ncu summary, when it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "spmv_dacsr16_f64_laplace3d_128.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    if rec.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu_index),
+                                      f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([c.strip() for c in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 5 + k and r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def cpu_oracle_baseline(rp, off, val, x, budget_s=10.0):
+    """The plain-C Listing 2 oracle (DA-CSR-16, FP64) on all host cores in the
+    affinity mask, repeated whole SpMVs for about budget_s seconds."""
+    from oracle import c_listing2 as C
+    cores = len(os.sched_getaffinity(0))
+    n = len(rp) - 1
+    y = np.zeros(n)
+    C.spmv_dacsr16(n, rp, off, val, x, out=y, nthreads=cores)  # warm-up
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        C.spmv_dacsr16(n, rp, off, val, x, out=y, nthreads=cores)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return el / reps, reps, cores
+
+
+def build_inputs():
+    import workloads as W
+    rp, col, val = W.laplace3d_7pt(GRID)
+    x = W.uniform_vector(GRID ** 3, W.rng_for(2, 0))
+    return rp, col, val, x
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    rp, col, val, x = build_inputs()
+    n, nnz = len(rp) - 1, len(col)
+    from oracle import c_listing2 as C
+    from oracle import dacsr as OD
+    off = OD.translate(n, rp, col).astype(np.int16)
+    cores = len(os.sched_getaffinity(0))
+    y = np.zeros(n)
+    for _ in range(max(args.warmup, 1)):
+        C.spmv_dacsr16(n, rp, off, val, x, out=y, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        C.spmv_dacsr16(n, rp, off, val, x, out=y, nthreads=cores)
+    t = (time.perf_counter() - t0) / args.steps
+    b = spmv_bytes(n, nnz, 2, 8, 8)
+    v = b / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 2), "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "nnz": nnz},
+            "cpu_baseline": {"value": round(v, 2), "unit": "GB/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{args.steps} whole DA-CSR-16 SpMVs (plain C Listing 2, "
+                                       f"OpenMP static rows) of the full workload"},
+            "e2e": {"value": round(v, 2), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_2307_06305_gb300 import damn as D
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    rp, col, val, x = build_inputs()
+    n, nnz = len(rp) - 1, len(col)
+    t_rp = [torch.from_numpy(rp).to(dev) for _ in range(NCOPY)]
+    t_col = [torch.from_numpy(col).to(dev) for _ in range(NCOPY)]
+    t_val = [torch.from_numpy(val).to(dev) for _ in range(NCOPY)]
+    t_off = []
+    for c in range(NCOPY):
+        off, info = D.damn_csr_to_dacsr(t_rp[c], t_col[c], n, raise_on_nofit=True)
+        t_off.append(off)
+    t_x = torch.from_numpy(x).to(dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    plans = [D.Plan(t_rp[c], nnz, n, torch.float64, idx=t_off[c]) for c in range(NCOPY)]
+    plans[0].autotune(D.DAMN_FMT_DACSR16, t_off[0], t_val[0], t_x, y)
+    tiling = plans[0].describe()["tiling"]
+    for c in range(1, NCOPY):
+        plans[c].set_tiling(tiling)
+    stream = torch.cuda.current_stream()
+
+    def step_da(i):
+        c = i % NCOPY
+        D.damn_spmv_dacsr16(t_rp[c], t_off[c], t_val[c], t_x, y, plan=plans[c])
+
+    def step_csr(i):
+        c = i % NCOPY
+        D.damn_spmv_csr32(t_rp[c], t_col[c], t_val[c], t_x, y, plan=plans[c])
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps, warmup):
+        for i in range(warmup):
+            fn(i)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            fn(i)
+        e1.record(stream)
+        barrier()
+        t = e0.elapsed_time(e1) * 1e-3
+        if dist is not None:
+            tt = torch.tensor([t], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t
+
+    clk = ClockSampler(local).__enter__()  # sampled across every timed phase below
+    t_da = timed(step_da, args.steps, args.warmup)
+    t_cs = timed(step_csr, args.steps, args.warmup)
+    if D.damn_device_status() != 0:
+        raise RuntimeError("device status word reports a timed-out wait")
+
+    b_da = spmv_bytes(n, nnz, 2, 8, 8)
+    b_cs = spmv_bytes(n, nnz, 4, 8, 8)
+    per_step_da = t_da / args.steps
+    per_step_cs = t_cs / args.steps
+    value = world * b_da / per_step_da / 1e9
+
+    # reduced-precision values (FP32 / BF16 values, FP32 vectors)
+    mixed = {}
+    for name, dt, vb in (("f32", torch.float32, 4), ("bf16", torch.bfloat16, 2)):
+        vals = [D.damn_cast_values(t_val[c], dt) for c in range(NCOPY)]
+        x32 = t_x.float()
+        y32 = torch.empty(n, dtype=torch.float32, device=dev)
+        pl = [D.Plan(t_rp[c], nnz, n, dt, idx=t_off[c]) for c in range(NCOPY)]
+
+        def step_m(i, vals=vals, pl=pl, x32=x32, y32=y32):
+            c = i % NCOPY
+            D.damn_spmv_dacsr16(t_rp[c], t_off[c], vals[c], x32, y32, plan=pl[c])
+        tm = timed(step_m, args.steps, args.warmup) / args.steps
+        bm = spmv_bytes(n, nnz, 2, vb, 4)
+        mixed[name] = {"gbs": round(bm / tm / 1e9, 1), "us": round(tm * 1e6, 2),
+                       "bytes": bm}
+        del vals, pl
+
+    # end to end through the public API: pinned host x -> device, SpMV, y -> host
+    hx = torch.from_numpy(x).pin_memory()
+    hy = torch.empty(n, dtype=torch.float64).pin_memory()
+    dx = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def step_e2e(i):
+        c = i % NCOPY
+        dx.copy_(hx, non_blocking=True)
+        D.damn_spmv_dacsr16(t_rp[c], t_off[c], t_val[c], dx, y, plan=plans[c])
+        hy.copy_(y, non_blocking=True)
+
+    e2e_steps = max(10, args.steps // 4)
+    t_e2e = timed(step_e2e, e2e_steps, min(args.warmup, 5)) / e2e_steps
+    e2e_value = world * b_da / t_e2e / 1e9
+    clk.__exit__(None, None, None)
+
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = b_da / per_step_da / 1e9
+    traffic = recorded_traffic()
+    desc = plans[0].describe()
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_step_da * 1e3, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "half_bandwidth": GRID * GRID,
+                   "l2": f"steps cycle over {NCOPY} matrix copies "
+                         f"({NCOPY * b_da / 1e6:.0f} MB > 126 MB L2)",
+                   "parallelism": f"replicas{world}",
+                   "plan": {k: desc[k] for k in ("tiling", "ntiles", "grid", "stages", "threads",
+                                                 "x_staged_tiles")}},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
+                     "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                     "algorithmic_bytes_per_launch": b_da},
+        "csr32": {"gbs": round(b_cs / per_step_cs / 1e9, 1), "us": round(per_step_cs * 1e6, 2),
+                  "speedup_da16_over_csr32": round(per_step_cs / per_step_da, 4),
+                  "model_speedup": round(b_cs / b_da, 4)},
+        "da16_us": round(per_step_da * 1e6, 2),
+        "mixed_precision_spmv": mixed,
+        "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n, "us_per_step": round(t_e2e * 1e6, 2)},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        from oracle import dacsr as OD
+        t_cpu, reps, cores = cpu_oracle_baseline(rp, OD.translate(n, rp, col).astype(np.int16),
+                                                 val, x, args.cpu_budget)
+        line["cpu_baseline"] = {"value": round(b_da / t_cpu / 1e9, 2), "unit": "GB/s",
+                                "cores": cores, "kind": "oracle",
+                                "sample": f"{reps} whole DA-CSR-16 SpMVs of the full workload "
+                                          f"(plain C Listing 2, OpenMP static rows), "
+                                          f"{t_cpu * reps:.1f} s"}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

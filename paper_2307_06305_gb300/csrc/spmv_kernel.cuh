@@ -26,10 +26,9 @@
 // Two compute modes keep FP64 FMA lanes dense:
 //
 //  mode 0 (one row per thread): thread i owns row i of the tile and runs the
-//    row's FMA chain in stored order.  Each warp loads its rows of tile j+1
-//    (values and x into registers, then hands the stage back) before running
-//    the FMAs of tile j; the warps do not wait for each other.  For rows of
-//    nearly equal length.
+//    row's FMA chain in stored order.  Each warp loads its rows (values and x
+//    into registers), hands the stage back, then runs the FMAs; the warps do
+//    not wait for each other.  For rows of nearly equal length.
 //  mode 1 (balanced slices): the tile's m entries are cut into NT contiguous
 //    slices of ceil(m/NT); every thread runs exactly its slice's FMAs,
 //    writing finished rows to shared memory and the partial sum of a row that
@@ -487,23 +486,13 @@ template <bool PLAIN, typename V, typename I, class C>
 __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char *smem,
                                              uint64_t *full, uint64_t *empty, const TileHdr *hdr,
                                              int ctid, double &dsum) {
-  // While the FMAs of tile j run, tile j+1 is already loaded into the other
-  // register set (warps do not wait for each other).
-  RowWork<V, I> w0, w1;
-  auto has = [&](int jj) {
-    return (long long)blockIdx.x + (long long)jj * gridDim.x < p.ntiles;
-  };
+  // Each warp loads its rows of a tile into registers, hands the stage back,
+  // then runs the FMA chains; the warps do not wait for each other.
+  RowWork<V, I> w;
   int j = 0;
-  if (!has(0) || !fetch_rows<V, I, C>(p, smem, full, empty, hdr, 0, ctid, w0)) return;
-  while (true) {
-    const bool v1 = has(j + 1) && fetch_rows<V, I, C>(p, smem, full, empty, hdr, j + 1, ctid, w1);
-    finish_rows<PLAIN, V, I, C>(p, smem, empty, hdr, ctid, w0, dsum);
-    if (!v1) return;
-    ++j;
-    const bool v0 = has(j + 1) && fetch_rows<V, I, C>(p, smem, full, empty, hdr, j + 1, ctid, w0);
-    finish_rows<PLAIN, V, I, C>(p, smem, empty, hdr, ctid, w1, dsum);
-    if (!v0) return;
-    ++j;
+  for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++j) {
+    if (!fetch_rows<V, I, C>(p, smem, full, empty, hdr, j, ctid, w)) return;
+    finish_rows<PLAIN, V, I, C>(p, smem, empty, hdr, ctid, w, dsum);
   }
 }
 
