@@ -106,6 +106,24 @@ int damn_csr_to_dacsr(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *
                       const int32_t *col, int16_t *off_out, damn_fit_info *h_info,
                       void *workspace, size_t ws_bytes, void *stream);
 
+/* Allocation-free variant of damn_csr_to_dacsr (the paper has no counterpart
+ * to this entry point).  For callers that cannot allocate device memory: an
+ * application or framework that owns every device allocation through its own
+ * pool, or a latency-critical loop where cudaMalloc (which can synchronise
+ * the whole device) is not acceptable.  Same arguments and results as
+ * damn_csr_to_dacsr minus the workspace: its scratch is a static array inside
+ * the library (about 64 KiB on every device that loads the library, held until
+ * the process exits), which limits nrows to DAMN_NOALLOC_MAX_ROWS; larger
+ * matrices are rejected with DAMN_ERR_INVALID_ARG.  The first call on a device
+ * looks up the array's device address, so make that first call before any
+ * stream capture.  Every call uses the same array: calls that overlap on the
+ * GPU (other streams or host threads without ordering between them) race.
+ * Synchronises stream; calls no allocator. */
+#define DAMN_NOALLOC_MAX_ROWS 1048576
+int damn_csr_to_dacsr_noalloc(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                              const int32_t *col, int16_t *off_out, damn_fit_info *h_info,
+                              void *stream);
+
 /* Workspace bytes needed by damn_validate_csr. */
 size_t damn_validate_csr_workspace_size(void);
 

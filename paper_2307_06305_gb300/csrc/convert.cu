@@ -9,6 +9,7 @@
 // read + 2 bytes written per entry, plus 4 bytes per row).
 #include <algorithm>
 #include <climits>
+#include <mutex>
 
 #include "damn_common.cuh"
 
@@ -242,5 +243,179 @@ extern "C" int damn_cast_values(int64_t n, const void *src, int src_dtype, void 
   const int blocks = (int)std::min<int64_t>(8LL * sm_count(), (n + 255) / 256);
   k_cast<<<blocks, 256, 0, s>>>(n, src, src_dtype, dst, dst_dtype);
   DAMN_CHECK_LAUNCH("k_cast");
+  return DAMN_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Allocation-free conversion (no counterpart in the paper)
+// ----------------------------------------------------------------------------
+// Some callers cannot allocate device memory: a host application or framework
+// that owns every device allocation through its own pool and forbids others,
+// or a latency-critical loop where cudaMalloc (which can synchronise the whole
+// device) is not acceptable.  damn_csr_to_dacsr_noalloc gives them the
+// conversion without a workspace: its scratch -- one fit record per block of
+// kRowsPerBlock rows plus one for the reduced result -- is a file-scope
+// device array that every GPU loading the library holds until the process
+// exits (kNoAllocMaxBlocks + 1 records of 32 bytes, about 64 KiB per device).
+namespace damn {
+namespace {
+
+constexpr int kNoAllocMaxBlocks = 2048;  // at most 2048 * 512 = 1,048,576 rows
+
+struct __align__(32) FitPartial {
+  int min_off;
+  int max_off;
+  unsigned long long n_fit;
+  unsigned long long n_bad;
+  int pad[2];
+};
+
+static __device__ __align__(256) FitPartial g_noalloc_fit[kNoAllocMaxBlocks + 1];
+
+// Same per-entry work as k_csr_to_dacsr16; the block's result is written to
+// its own record instead of being combined with atomics.
+__global__ void __launch_bounds__(kConvThreads)
+k_csr_to_dacsr16_part(int nrows, int ncols, const int *__restrict__ rowptr,
+                      const int *__restrict__ col, int16_t *__restrict__ off, FitPartial *part) {
+  __shared__ int rp[kRowsPerBlock + 1];
+  __shared__ int s_mn[kConvThreads / 32], s_mx[kConvThreads / 32];
+  __shared__ unsigned long long s_nf[kConvThreads / 32], s_nb[kConvThreads / 32];
+  const int r0 = blockIdx.x * kRowsPerBlock;
+  const int nr = min(kRowsPerBlock, nrows - r0);
+  for (int i = threadIdx.x; i <= nr; i += kConvThreads) rp[i] = rowptr[r0 + i];
+  __syncthreads();
+  const int k0 = rp[0], k1 = rp[nr];
+  int mn = INT_MAX, mx = INT_MIN;
+  unsigned long long nf = 0, nb = 0;
+  for (int k = k0 + threadIdx.x; k < k1; k += kConvThreads) {
+    const int lr = row_of(rp, nr, k);
+    const int c = __ldcs(col + k);
+    const int d = c - (r0 + lr);
+    __stcs(off + k, static_cast<int16_t>(d));
+    mn = min(mn, d);
+    mx = max(mx, d);
+    nf += (d >= -32768 && d <= 32767) ? 1ull : 0ull;
+    nb += (c < 0 || c >= ncols) ? 1ull : 0ull;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    nf += __shfl_xor_sync(0xffffffffu, nf, o);
+    nb += __shfl_xor_sync(0xffffffffu, nb, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { s_mn[w] = mn; s_mx[w] = mx; s_nf[w] = nf; s_nb[w] = nb; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < kConvThreads / 32; ++i) {
+      mn = min(mn, s_mn[i]); mx = max(mx, s_mx[i]); nf += s_nf[i]; nb += s_nb[i];
+    }
+    FitPartial r;
+    r.min_off = mn; r.max_off = mx; r.n_fit = nf; r.n_bad = nb; r.pad[0] = r.pad[1] = 0;
+    part[blockIdx.x] = r;
+  }
+}
+
+// Combines the nblocks records into *out (written, not accumulated, so
+// nothing from an earlier call survives into this one).
+__global__ void k_fit_reduce_part(const FitPartial *part, int nblocks, FitPartial *out) {
+  __shared__ int s_mn[32], s_mx[32];
+  __shared__ unsigned long long s_nf[32], s_nb[32];
+  int mn = INT_MAX, mx = INT_MIN;
+  unsigned long long nf = 0, nb = 0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    mn = min(mn, part[b].min_off);
+    mx = max(mx, part[b].max_off);
+    nf += part[b].n_fit;
+    nb += part[b].n_bad;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    nf += __shfl_xor_sync(0xffffffffu, nf, o);
+    nb += __shfl_xor_sync(0xffffffffu, nb, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { s_mn[w] = mn; s_mx[w] = mx; s_nf[w] = nf; s_nb[w] = nb; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x / 32); ++i) {
+      mn = min(mn, s_mn[i]); mx = max(mx, s_mx[i]); nf += s_nf[i]; nb += s_nb[i];
+    }
+    FitPartial r;
+    r.min_off = mn; r.max_off = mx; r.n_fit = nf; r.n_bad = nb; r.pad[0] = r.pad[1] = 0;
+    *out = r;
+  }
+}
+
+// Device address of g_noalloc_fit on the current device, looked up once per
+// device.  In host code the array's name is only a stand-in for the symbol,
+// so kernels get this address, never the name.
+FitPartial *noalloc_fit_scratch(int *rc) {
+  static FitPartial *addr[64];
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) { *rc = cuda_error(e, "damn_csr_to_dacsr_noalloc: cudaGetDevice"); return nullptr; }
+  if (dev < 0 || dev >= 64) {
+    *rc = set_error(DAMN_ERR_UNSUPPORTED, "damn_csr_to_dacsr_noalloc: device index %d", dev);
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_fit);
+    if (e != cudaSuccess) {
+      *rc = cuda_error(e, "damn_csr_to_dacsr_noalloc: cudaGetSymbolAddress");
+      return nullptr;
+    }
+    addr[dev] = static_cast<FitPartial *>(p);
+  }
+  return addr[dev];
+}
+
+}  // namespace
+}  // namespace damn
+
+extern "C" int damn_csr_to_dacsr_noalloc(int32_t nrows, int32_t ncols, int64_t nnz,
+                                         const int32_t *rowptr, const int32_t *col,
+                                         int16_t *off_out, damn_fit_info *h_info, void *stream) {
+  if (nrows < 0 || ncols < 0 || nnz < 0 || nnz > INT_MAX)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_csr_to_dacsr_noalloc: bad sizes");
+  const long long max_rows = (long long)kNoAllocMaxBlocks * kRowsPerBlock;
+  if (nrows > max_rows)
+    return set_error(DAMN_ERR_INVALID_ARG,
+                     "damn_csr_to_dacsr_noalloc: %d rows exceed the %lld rows its static scratch "
+                     "covers; use damn_csr_to_dacsr with a workspace",
+                     nrows, max_rows);
+  if (!h_info || !rowptr || (nnz > 0 && (!col || !off_out)))
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_csr_to_dacsr_noalloc: NULL pointer");
+  int rc = DAMN_OK;
+  FitPartial *part = noalloc_fit_scratch(&rc);
+  if (!part) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int blocks = (nrows + kRowsPerBlock - 1) / kRowsPerBlock;
+  if (blocks > 0) {
+    k_csr_to_dacsr16_part<<<blocks, kConvThreads, 0, s>>>(nrows, ncols, rowptr, col, off_out, part);
+    DAMN_CHECK_LAUNCH("k_csr_to_dacsr16_part");
+  }
+  k_fit_reduce_part<<<1, 256, 0, s>>>(part, blocks, part + kNoAllocMaxBlocks);
+  DAMN_CHECK_LAUNCH("k_fit_reduce_part");
+  FitPartial h{};
+  DAMN_CUDA(cudaMemcpyAsync(&h, part + kNoAllocMaxBlocks, sizeof(h), cudaMemcpyDeviceToHost, s));
+  DAMN_CUDA(cudaStreamSynchronize(s));
+  if (nnz == 0) { h.min_off = 0; h.max_off = 0; }
+  h_info->min_off = h.min_off;
+  h_info->max_off = h.max_off;
+  h_info->w = std::max<int64_t>(-(int64_t)h.min_off, (int64_t)h.max_off);
+  h_info->n_fit = static_cast<int64_t>(h.n_fit);
+  h_info->n_bad = static_cast<int64_t>(h.n_bad);
+  h_info->fits = (static_cast<int64_t>(h.n_fit) == nnz && h.n_bad == 0) ? 1 : 0;
+  h_info->reserved = 0;
+  if (!h_info->fits)
+    return set_error(DAMN_ERR_NOFIT,
+                     "damn_csr_to_dacsr_noalloc: %lld of %lld entries do not fit int16 (min %d, max %d), %lld bad columns",
+                     (long long)(nnz - h_info->n_fit), (long long)nnz, h.min_off, h.max_off,
+                     (long long)h.n_bad);
   return DAMN_OK;
 }

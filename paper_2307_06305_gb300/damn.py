@@ -97,6 +97,8 @@ _sig("damn_selftest_wait_timeout", ctypes.c_int, [I64, P])
 _sig("damn_csr_to_dacsr_workspace_size", SZ, [])
 _sig("damn_csr_to_dacsr", ctypes.c_int,
      [I32, I32, I64, P, P, P, ctypes.POINTER(damn_fit_info), P, SZ, P])
+_sig("damn_csr_to_dacsr_noalloc", ctypes.c_int,
+     [I32, I32, I64, P, P, P, ctypes.POINTER(damn_fit_info), P])
 _sig("damn_validate_csr_workspace_size", SZ, [])
 _sig("damn_validate_csr", ctypes.c_int,
      [I32, I32, I64, P, P, ctypes.POINTER(I64), ctypes.POINTER(I64), P, SZ, P])
@@ -223,6 +225,25 @@ def damn_csr_to_dacsr(rowptr: torch.Tensor, col: torch.Tensor, ncols: int, off_o
     rc = _lib.damn_csr_to_dacsr(nrows, int(ncols), nnz, _ptr(rowptr), _ptr(col), _ptr(off_out),
                                 ctypes.byref(info), _ptr(ws), ws.numel(), _stream(stream))
     _check(rc, "damn_csr_to_dacsr", allow=() if raise_on_nofit else (DAMN_ERR_NOFIT,))
+    return off_out, FitInfo(info.min_off, info.max_off, info.w, info.n_fit, info.n_bad,
+                            bool(info.fits))
+
+
+DAMN_NOALLOC_MAX_ROWS = 1048576
+
+
+def damn_csr_to_dacsr_noalloc(rowptr: torch.Tensor, col: torch.Tensor, ncols: int,
+                              off_out: torch.Tensor, stream=None, raise_on_nofit: bool = False):
+    """CSR -> DA-CSR-16 without any device allocation, for callers that
+    cannot allocate (their framework owns all device memory, or cudaMalloc's
+    device-wide synchronisation is not acceptable on their path).  The
+    caller provides ``off_out``; the library's static scratch limits the
+    matrix to DAMN_NOALLOC_MAX_ROWS rows.  Returns (off_out, FitInfo)."""
+    nrows = rowptr.numel() - 1
+    info = damn_fit_info()
+    rc = _lib.damn_csr_to_dacsr_noalloc(nrows, int(ncols), col.numel(), _ptr(rowptr), _ptr(col),
+                                        _ptr(off_out), ctypes.byref(info), _stream(stream))
+    _check(rc, "damn_csr_to_dacsr_noalloc", allow=() if raise_on_nofit else (DAMN_ERR_NOFIT,))
     return off_out, FitInfo(info.min_off, info.max_off, info.w, info.n_fit, info.n_bad,
                             bool(info.fits))
 
