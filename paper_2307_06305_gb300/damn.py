@@ -343,3 +343,45 @@ def damn_spmv_dacsr16(rowptr, off, val, x, y, alpha=1.0, beta=0.0, plan=None, nc
                                 float(beta), _plan_handle(plan), _stream(stream))
     _check(rc, "damn_spmv_dacsr16")
     return y
+
+
+# ----------------------------------------------------------------------------
+# a6: CG and CG-IR
+# ----------------------------------------------------------------------------
+
+def _cg_result(res, rc):
+    return {"iterations": int(res.iterations), "outer": int(res.outer),
+            "converged": bool(res.converged), "relres": float(res.relres),
+            "true_relres": float(res.true_relres), "status": int(rc)}
+
+
+def damn_cg(rowptr, off, val, b, x, rtol=1e-10, max_iter=1000, plan=None, stream=None,
+            workspace=None):
+    """FP64 CG on a DA-CSR-16 SPD matrix; x holds x0 on entry and the solution
+    on exit.  Returns a dict (iterations, converged, relres, true_relres)."""
+    n = rowptr.numel() - 1
+    need = _fn("damn_cg_workspace_size")(n)
+    ws = workspace if workspace is not None else _workspace(need, b.device)
+    res = damn_cg_result()
+    rc = _fn("damn_cg")(n, off.numel(), _ptr(rowptr), _ptr(off), _ptr(val), _ptr(b), _ptr(x),
+                        float(rtol), int(max_iter), _plan_handle(plan), ctypes.byref(res), _ptr(ws),
+                        ws.numel(), _stream(stream))
+    _check(rc, "damn_cg", allow=(DAMN_ERR_NOT_CONVERGED,))
+    return _cg_result(res, rc)
+
+
+def damn_cg_ir(rowptr, off, val, val_low, b, x, rtol=1e-10, inner_rtol=1e-3, max_inner=100,
+               max_outer=50, plan64=None, plan_low=None, stream=None, workspace=None):
+    """Mixed-precision refinement: FP64 residual / update, inner CG with
+    val_low (float32 or bfloat16 values), FP32 vectors and FP64 dots."""
+    n = rowptr.numel() - 1
+    need = _fn("damn_cg_ir_workspace_size")(n)
+    ws = workspace if workspace is not None else _workspace(need, b.device)
+    res = damn_cg_result()
+    rc = _fn("damn_cg_ir")(n, off.numel(), _ptr(rowptr), _ptr(off), _ptr(val), _ptr(val_low),
+                           _DTYPE_CODE[val_low.dtype], _ptr(b), _ptr(x), float(rtol),
+                           float(inner_rtol), int(max_inner), int(max_outer), _plan_handle(plan64),
+                           _plan_handle(plan_low), ctypes.byref(res), _ptr(ws), ws.numel(),
+                           _stream(stream))
+    _check(rc, "damn_cg_ir", allow=(DAMN_ERR_NOT_CONVERGED,))
+    return _cg_result(res, rc)
