@@ -1,0 +1,366 @@
+// Multi-right-hand-side products Y = A X for DA-CSR-16 matrices, singly and
+// for a whole batch of independent matrices in one persistent launch.
+//
+// For each matrix, X is row-major ncols x k and Y row-major nrows x k; entry
+// i of row r multiplies row r + off[i] of X (the shifted view of Listing 2,
+// Section 4, applied to each column of X).
+//
+// Work decomposition: a warp takes R = 32 / L rows at a time, L = the largest
+// power of two <= min(k, 32) lanes per row; lane l of a row group owns the
+// right-hand-side columns l, l + L, ... (at most two), so every FMA lane does
+// useful work and the X loads of a row group are contiguous.  Each lane walks
+// its row's entries in stored order (Listing 2 order per column), four at a
+// time so that four entries' loads are in flight.
+//
+// Batched launch: the host builds a list of (matrix, first row) work items
+// of rows_per_item rows each; persistent warps take items round-robin.  The
+// plan's autotuner times a few (rows_per_item, threads) shapes on the real
+// operands and keeps the fastest; the launch is captured in a CUDA graph.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <vector>
+
+#include "damn_common.cuh"
+
+namespace damn {
+namespace {
+
+struct DevDesc {  // device copy of damn_mat_desc
+  int nrows, ncols;
+  long long nnz;
+  const int *rowptr;
+  const int16_t *off;
+  const void *val;
+  const void *X;
+  void *Y;
+};
+
+// y[row, jcols] for one row group; T: FP64 or FP32 (values and vectors)
+template <typename T, int L, int J>
+__device__ __forceinline__ void spmm_row(const DevDesc &d, int row, int k, int li) {
+  const T *val = static_cast<const T *>(d.val);
+  const T *X = static_cast<const T *>(d.X);
+  T *Y = static_cast<T *>(d.Y);
+  const int b = __ldg(d.rowptr + row), e = __ldg(d.rowptr + row + 1);
+  T acc[J];
+#pragma unroll
+  for (int jj = 0; jj < J; ++jj) acc[jj] = T(0);
+  constexpr int U = 4;
+  for (int q = b; q < e; q += U) {
+    T v[U];
+    int c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      v[u] = T(0);
+      c[u] = row;
+      if (q + u < e) {
+        v[u] = __ldg(val + q + u);
+        c[u] = row + static_cast<int>(__ldg(d.off + q + u));
+      }
+    }
+    T xv[U][J];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int jj = 0; jj < J; ++jj) {
+        const int j = li + jj * L;
+        xv[u][jj] = (q + u < e && j < k) ? __ldg(X + (size_t)c[u] * k + j) : T(0);
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (q + u < e)
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) acc[jj] = fma_acc(v[u], xv[u][jj], acc[jj]);
+  }
+#pragma unroll
+  for (int jj = 0; jj < J; ++jj) {
+    const int j = li + jj * L;
+    if (j < k) Y[(size_t)row * k + j] = acc[jj];
+  }
+}
+
+// Batched: items[i] = {matrix, first row}; rows_per_item rows per item.
+template <typename T, int L, int J>
+__global__ void k_spmm_batched(const DevDesc *descs, const int2 *items, int nitems, int k,
+                               int rows_per_item) {
+  constexpr int R = 32 / L;
+  const int lane = threadIdx.x & 31, grp = lane / L, li = lane % L;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long it = warp; it < nitems; it += nwarps) {
+    const int2 item = items[it];
+    const DevDesc d = descs[item.x];
+    const int rend = min(item.y + rows_per_item, d.nrows);
+    for (int row = item.y + grp; row < rend; row += R) spmm_row<T, L, J>(d, row, k, li);
+  }
+}
+
+// One matrix: the rows are the work, no descriptor array.
+template <typename T, int L, int J>
+__global__ void k_spmm_single(DevDesc d, int k) {
+  constexpr int R = 32 / L;
+  const int lane = threadIdx.x & 31, grp = lane / L, li = lane % L;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long row = warp * R + grp; row < d.nrows; row += nwarps * R)
+    spmm_row<T, L, J>(d, static_cast<int>(row), k, li);
+}
+
+int lanes_for(int k) {
+  int L = 1;
+  while (L * 2 <= std::min(k, 32)) L *= 2;
+  return L;
+}
+
+template <typename T, int L>
+int launch_single_l(const DevDesc &d, int k, cudaStream_t s) {
+  const int R = 32 / L;
+  const long long warps_needed = (d.nrows + R - 1) / R;
+  const int threads = 256;
+  const int blocks = (int)std::max(1LL, std::min<long long>(8LL * sm_count(),
+                                                            (warps_needed * 32 + threads - 1) / threads));
+  if ((k + L - 1) / L <= 1)
+    k_spmm_single<T, L, 1><<<blocks, threads, 0, s>>>(d, k);
+  else
+    k_spmm_single<T, L, 2><<<blocks, threads, 0, s>>>(d, k);
+  DAMN_CHECK_LAUNCH("k_spmm_single");
+  return DAMN_OK;
+}
+
+template <typename T>
+int launch_single(const DevDesc &d, int k, cudaStream_t s) {
+  switch (lanes_for(k)) {
+    case 1: return launch_single_l<T, 1>(d, k, s);
+    case 2: return launch_single_l<T, 2>(d, k, s);
+    case 4: return launch_single_l<T, 4>(d, k, s);
+    case 8: return launch_single_l<T, 8>(d, k, s);
+    case 16: return launch_single_l<T, 16>(d, k, s);
+    default: return launch_single_l<T, 32>(d, k, s);
+  }
+}
+
+template <typename T, int L>
+int launch_batched_l(const DevDesc *descs, const int2 *items, int nitems, int k, int rpi,
+                     int blocks, int threads, cudaStream_t s) {
+  if ((k + L - 1) / L <= 1)
+    k_spmm_batched<T, L, 1><<<blocks, threads, 0, s>>>(descs, items, nitems, k, rpi);
+  else
+    k_spmm_batched<T, L, 2><<<blocks, threads, 0, s>>>(descs, items, nitems, k, rpi);
+  DAMN_CHECK_LAUNCH("k_spmm_batched");
+  return DAMN_OK;
+}
+
+template <typename T>
+int launch_batched(const DevDesc *descs, const int2 *items, int nitems, int k, int rpi, int blocks,
+                   int threads, cudaStream_t s) {
+  switch (lanes_for(k)) {
+    case 1: return launch_batched_l<T, 1>(descs, items, nitems, k, rpi, blocks, threads, s);
+    case 2: return launch_batched_l<T, 2>(descs, items, nitems, k, rpi, blocks, threads, s);
+    case 4: return launch_batched_l<T, 4>(descs, items, nitems, k, rpi, blocks, threads, s);
+    case 8: return launch_batched_l<T, 8>(descs, items, nitems, k, rpi, blocks, threads, s);
+    case 16: return launch_batched_l<T, 16>(descs, items, nitems, k, rpi, blocks, threads, s);
+    default: return launch_batched_l<T, 32>(descs, items, nitems, k, rpi, blocks, threads, s);
+  }
+}
+
+bool desc_ok(const damn_mat_desc &m) {
+  if (m.nrows < 0 || m.ncols < 0 || m.nnz < 0 || m.nnz > INT_MAX) return false;
+  if (m.nrows > 0 && (!m.rowptr || !m.Y)) return false;
+  if (m.nnz > 0 && (!m.off || !m.val || !m.X)) return false;
+  return true;
+}
+
+}  // namespace
+}  // namespace damn
+
+using namespace damn;
+
+struct damn_batch_plan {
+  int count, k, dtype;
+  DevDesc *d_descs;
+  int2 *d_items;
+  int nitems;
+  int rows_per_item;
+  int threads, blocks;
+  std::vector<int> nrows;  // per matrix, to rebuild items
+  cudaGraphExec_t graph;
+  double tune_ms;
+};
+
+static int batch_build_items(damn_batch_plan *pl, int rpi) {
+  std::vector<int2> items;
+  for (int m = 0; m < pl->count; ++m)
+    for (int r = 0; r < pl->nrows[m]; r += rpi) items.push_back(make_int2(m, r));
+  if (pl->d_items) cudaFree(pl->d_items);
+  pl->d_items = nullptr;
+  pl->nitems = (int)items.size();
+  pl->rows_per_item = rpi;
+  if (items.empty()) return DAMN_OK;
+  DAMN_CUDA(cudaMalloc(&pl->d_items, sizeof(int2) * items.size()));
+  DAMN_CUDA(cudaMemcpy(pl->d_items, items.data(), sizeof(int2) * items.size(),
+                       cudaMemcpyHostToDevice));
+  return DAMN_OK;
+}
+
+static int batch_launch(const damn_batch_plan *pl, cudaStream_t s) {
+  if (pl->nitems == 0) return DAMN_OK;
+  if (pl->dtype == DAMN_F64)
+    return launch_batched<double>(pl->d_descs, pl->d_items, pl->nitems, pl->k, pl->rows_per_item,
+                                  pl->blocks, pl->threads, s);
+  return launch_batched<float>(pl->d_descs, pl->d_items, pl->nitems, pl->k, pl->rows_per_item,
+                               pl->blocks, pl->threads, s);
+}
+
+static void batch_free(damn_batch_plan *pl) {
+  if (pl->graph) cudaGraphExecDestroy(pl->graph);
+  if (pl->d_items) cudaFree(pl->d_items);
+  if (pl->d_descs) cudaFree(pl->d_descs);
+  pl->graph = nullptr;
+  pl->d_items = nullptr;
+  pl->d_descs = nullptr;
+}
+
+extern "C" int damn_spmm_dacsr16(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                                 const int16_t *off, const void *val, int dtype, int32_t k,
+                                 const void *X, void *Y, void *stream) {
+  damn_mat_desc m{nrows, ncols, nnz, rowptr, off, val, X, Y};
+  if (!desc_ok(m)) return set_error(DAMN_ERR_INVALID_ARG, "damn_spmm_dacsr16: bad arguments");
+  if (dtype != DAMN_F64 && dtype != DAMN_F32)
+    return set_error(DAMN_ERR_UNSUPPORTED, "damn_spmm_dacsr16: dtype must be DAMN_F64 or DAMN_F32");
+  if (k < 1 || k > 64) return set_error(DAMN_ERR_INVALID_ARG, "damn_spmm_dacsr16: k must be 1..64");
+  if (nrows == 0) return DAMN_OK;
+  DevDesc d{nrows, ncols, nnz, rowptr, off, val, X, Y};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return dtype == DAMN_F64 ? launch_single<double>(d, k, s) : launch_single<float>(d, k, s);
+}
+
+extern "C" int damn_batch_plan_create(int32_t count, const damn_mat_desc *h_descs, int32_t k,
+                                      int dtype, int autotune, void *stream,
+                                      damn_batch_plan **out) {
+  if (!out) return set_error(DAMN_ERR_INVALID_ARG, "damn_batch_plan_create: out is NULL");
+  *out = nullptr;
+  if (count < 0 || (count > 0 && !h_descs))
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_batch_plan_create: bad count / descriptors");
+  if (dtype != DAMN_F64 && dtype != DAMN_F32)
+    return set_error(DAMN_ERR_UNSUPPORTED, "damn_batch_plan_create: dtype must be F64 or F32");
+  if (k < 1 || k > 64) return set_error(DAMN_ERR_INVALID_ARG, "damn_batch_plan_create: k must be 1..64");
+  for (int m = 0; m < count; ++m)
+    if (!desc_ok(h_descs[m]))
+      return set_error(DAMN_ERR_INVALID_ARG, "damn_batch_plan_create: bad descriptor %d", m);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  damn_batch_plan *pl = new damn_batch_plan();
+  pl->count = count; pl->k = k; pl->dtype = dtype;
+  pl->d_descs = nullptr; pl->d_items = nullptr; pl->graph = nullptr; pl->tune_ms = 0.0;
+  pl->nrows.resize(count);
+  std::vector<DevDesc> dd(count);
+  for (int m = 0; m < count; ++m) {
+    const damn_mat_desc &h = h_descs[m];
+    dd[m] = DevDesc{h.nrows, h.ncols, h.nnz, h.rowptr, h.off, h.val, h.X, h.Y};
+    pl->nrows[m] = h.nrows;
+  }
+  auto fail = [&](int rc) { batch_free(pl); delete pl; return rc; };
+  if (count > 0) {
+    cudaError_t e = cudaMalloc(&pl->d_descs, sizeof(DevDesc) * count);
+    if (e != cudaSuccess) return fail(cuda_error(e, "damn_batch_plan_create: cudaMalloc"));
+    e = cudaMemcpy(pl->d_descs, dd.data(), sizeof(DevDesc) * count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(cuda_error(e, "damn_batch_plan_create: cudaMemcpy"));
+  }
+  // default shape: one row group of 32/L rows per warp pass, items of 256 rows
+  int rc = batch_build_items(pl, 256);
+  if (rc) return fail(rc);
+  pl->threads = 256;
+  pl->blocks = std::max(1, std::min(8 * sm_count(), (pl->nitems * 32 + 255) / 256));
+  if (autotune && pl->nitems > 0) {
+    const int rpis[3] = {64, 256, 1024};
+    const int tps[2] = {128, 256};
+    float best = 1e30f;
+    int best_rpi = 256, best_tp = 256;
+    cudaEvent_t e0, e1;
+    DAMN_CUDA(cudaEventCreate(&e0));
+    DAMN_CUDA(cudaEventCreate(&e1));
+    for (int a = 0; a < 3 && rc == DAMN_OK; ++a) {
+      rc = batch_build_items(pl, rpis[a]);
+      for (int b = 0; b < 2 && rc == DAMN_OK; ++b) {
+        pl->threads = tps[b];
+        const int warps_per_block = pl->threads / 32;
+        pl->blocks = std::max(1, std::min(16 * sm_count(),
+                                          (pl->nitems + warps_per_block - 1) / warps_per_block));
+        rc = batch_launch(pl, s);  // warm
+        float tmin = 1e30f;
+        for (int r = 0; r < 3 && rc == DAMN_OK; ++r) {
+          cudaEventRecord(e0, s);
+          rc = batch_launch(pl, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          tmin = std::min(tmin, ms);
+        }
+        if (tmin < best) { best = tmin; best_rpi = rpis[a]; best_tp = tps[b]; }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return fail(rc);
+    rc = batch_build_items(pl, best_rpi);
+    if (rc) return fail(rc);
+    pl->threads = best_tp;
+    const int wpb = pl->threads / 32;
+    pl->blocks = std::max(1, std::min(16 * sm_count(), (pl->nitems + wpb - 1) / wpb));
+    pl->tune_ms = best;
+  }
+  // capture the persistent launch in a graph
+  if (pl->nitems > 0) {
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(cuda_error(e, "cudaStreamCreate"));
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = batch_launch(pl, cs);
+      e = cudaStreamEndCapture(cs, &g);
+    }
+    if (e == cudaSuccess && rc == DAMN_OK) e = cudaGraphInstantiate(&pl->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (rc) return fail(rc);
+    if (e != cudaSuccess) return fail(cuda_error(e, "damn_batch_plan_create: graph"));
+  }
+  DAMN_CUDA(cudaStreamSynchronize(s));
+  *out = pl;
+  return DAMN_OK;
+}
+
+extern "C" int damn_batch_plan_describe(const damn_batch_plan *plan, damn_batch_desc *h) {
+  if (!plan || !h) return set_error(DAMN_ERR_INVALID_ARG, "damn_batch_plan_describe: NULL");
+  h->count = plan->count;
+  h->k = plan->k;
+  h->dtype = plan->dtype;
+  h->ntiles = plan->nitems;
+  h->grid = plan->blocks;
+  h->threads = plan->threads;
+  h->tile_items = plan->rows_per_item;
+  h->graph_ready = plan->graph ? 1 : 0;
+  h->tune_ms = plan->tune_ms;
+  return DAMN_OK;
+}
+
+extern "C" int damn_batch_plan_destroy(damn_batch_plan *plan) {
+  if (!plan) return DAMN_OK;
+  batch_free(plan);
+  delete plan;
+  return DAMN_OK;
+}
+
+extern "C" int damn_spmm_dacsr16_batched(const damn_batch_plan *plan, void *stream) {
+  if (!plan) return set_error(DAMN_ERR_INVALID_ARG, "damn_spmm_dacsr16_batched: plan is NULL");
+  return batch_launch(plan, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int damn_batch_graph_launch(damn_batch_plan *plan, void *stream) {
+  if (!plan) return set_error(DAMN_ERR_INVALID_ARG, "damn_batch_graph_launch: plan is NULL");
+  if (!plan->graph) return DAMN_OK;  // empty batch
+  DAMN_CUDA(cudaGraphLaunch(plan->graph, static_cast<cudaStream_t>(stream)));
+  return DAMN_OK;
+}

@@ -385,3 +385,61 @@ def damn_cg_ir(rowptr, off, val, val_low, b, x, rtol=1e-10, inner_rtol=1e-3, max
                            _stream(stream))
     _check(rc, "damn_cg_ir", allow=(DAMN_ERR_NOT_CONVERGED,))
     return _cg_result(res, rc)
+
+
+# ----------------------------------------------------------------------------
+# a7: multi-RHS SpMM, single and batched
+# ----------------------------------------------------------------------------
+
+def damn_spmm_dacsr16(rowptr, off, val, X, Y, stream=None):
+    """Y = A X for one DA-CSR-16 matrix; X [ncols, k], Y [nrows, k] row-major."""
+    nrows = rowptr.numel() - 1
+    k = X.shape[1]
+    rc = _fn("damn_spmm_dacsr16")(nrows, X.shape[0], off.numel(), _ptr(rowptr), _ptr(off),
+                                  _ptr(val), _DTYPE_CODE[val.dtype], k, _ptr(X), _ptr(Y),
+                                  _stream(stream))
+    _check(rc, "damn_spmm_dacsr16")
+    return Y
+
+
+class BatchPlan:
+    """A batch of independent products Y_m = A_m X_m (DA-CSR-16) run by one
+    persistent launch (and its captured CUDA graph).  ``mats`` is a list of
+    (rowptr, off, val, X, Y) tensors that must stay alive with the plan."""
+
+    def __init__(self, mats, k: int, dtype: torch.dtype, autotune: bool = True, stream=None):
+        self.mats = mats
+        arr = (damn_mat_desc * max(1, len(mats)))()
+        for i, (rp, off, val, X, Y) in enumerate(mats):
+            arr[i] = damn_mat_desc(rp.numel() - 1, X.shape[0], off.numel(), rp.data_ptr(),
+                                   off.data_ptr(), val.data_ptr(), X.data_ptr(), Y.data_ptr())
+        self.handle = P()
+        rc = _fn("damn_batch_plan_create")(len(mats), arr, int(k), _DTYPE_CODE[dtype],
+                                           int(bool(autotune)), _stream(stream),
+                                           ctypes.byref(self.handle))
+        _check(rc, "damn_batch_plan_create")
+
+    def launch(self, stream=None):
+        _check(_fn("damn_spmm_dacsr16_batched")(self.handle, _stream(stream)),
+               "damn_spmm_dacsr16_batched")
+
+    def graph_launch(self, stream=None):
+        _check(_fn("damn_batch_graph_launch")(self.handle, _stream(stream)),
+               "damn_batch_graph_launch")
+
+    def describe(self) -> dict:
+        d = damn_batch_desc()
+        _check(_fn("damn_batch_plan_describe")(self.handle, ctypes.byref(d)),
+               "damn_batch_plan_describe")
+        return {k: getattr(d, k) for k, _ in damn_batch_desc._fields_}
+
+    def close(self):
+        if self.handle:
+            _fn("damn_batch_plan_destroy")(self.handle)
+            self.handle = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
