@@ -66,9 +66,11 @@ const char *damn_last_error(void);
 /* Library version, major * 10000 + minor * 100 + patch. */
 int damn_version(void);
 
-/* Reads the library's device status word for the current device (DAMN_OK
- * or DAMN_ERR_TIMEOUT after a bounded wait inside a kernel gave up) into
- * *h_status and clears it when reset != 0.  Synchronises stream. */
+/* Reads the library's device status word for the current device into
+ * *h_status and clears it when reset != 0: DAMN_OK, DAMN_ERR_TIMEOUT after a
+ * bounded wait inside a kernel gave up, or DAMN_ERR_INVALID_ARG after
+ * damn_permute_sym found that perm is not a permutation or a column of A out
+ * of range.  The first error is kept until reset.  Synchronises stream. */
 int damn_device_status(int32_t *h_status, int reset, void *stream);
 
 /* Failure-detection self test: launches one kernel that waits on a device
@@ -162,7 +164,16 @@ size_t damn_permute_sym_workspace_size(int32_t n);
 /* B = P A P^T on the device: row i of B is row perm[i] of A, every column c
  * becomes iperm[c], and each row is sorted by new column (entries with equal
  * columns keep their stored order).  val/val_out have type dtype (F64, F32,
- * BF16; may be NULL to permute the pattern only).  Asynchronous. */
+ * BF16; val may be NULL to permute the pattern only).  All pointers except
+ * the workspace are device arrays owned by the caller: rowptr[n+1], col[nnz],
+ * perm[n] (new -> old), rowptr_out[n+1], col_out[nnz], val_out[nnz].
+ * rowptr must be a valid CSR row pointer with rowptr[n] == nnz <= INT32_MAX.
+ * workspace: device, 16-byte aligned, >= damn_permute_sym_workspace_size(n)
+ * bytes, no initial contents.  Asynchronous.  If perm is not a permutation
+ * of 0..n-1 (checked on the device) nothing is written to col_out/val_out
+ * and the device status word reports DAMN_ERR_INVALID_ARG; a column outside
+ * 0..n-1 is reported the same way and stored as INT32_MAX.  Cost: one warp
+ * per row, O(len^2 / 32) comparisons for a row of len entries. */
 int damn_permute_sym(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
                      const void *val, int dtype, const int32_t *perm, int32_t *rowptr_out,
                      int32_t *col_out, void *val_out, void *workspace, size_t ws_bytes,

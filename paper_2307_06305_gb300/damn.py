@@ -443,3 +443,60 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------
+# a2: RCM ordering and the symmetric permutation
+# ----------------------------------------------------------------------------
+
+def damn_rcm_order(h_rowptr, h_col):
+    """Host RCM ordering of a square pattern given as host (numpy int32)
+    arrays; returns (perm new->old int32, w_before, w_after)."""
+    import numpy as np
+    rp = np.ascontiguousarray(h_rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(h_col, dtype=np.int32)
+    n = rp.size - 1
+    perm = np.empty(max(n, 1), dtype=np.int32)
+    wb, wa = I64(0), I64(0)
+    rc = _fn("damn_rcm_order")(n, col.size, rp.ctypes.data, col.ctypes.data if col.size else None,
+                               perm.ctypes.data, ctypes.byref(wb), ctypes.byref(wa))
+    _check(rc, "damn_rcm_order")
+    return perm[:n], int(wb.value), int(wa.value)
+
+
+def _perm_outputs(n, nnz, val, device):
+    rp_out = torch.empty(n + 1, dtype=torch.int32, device=device)
+    col_out = torch.empty(max(nnz, 1), dtype=torch.int32, device=device)[:nnz]
+    val_out = None if val is None else torch.empty(max(nnz, 1), dtype=val.dtype, device=device)[:nnz]
+    return rp_out, col_out, val_out
+
+
+def damn_permute_sym(rowptr, col, val, perm, stream=None):
+    """B = P A P^T on the device; returns (rowptr_out, col_out, val_out)."""
+    n = rowptr.numel() - 1
+    nnz = col.numel()
+    rp_out, col_out, val_out = _perm_outputs(n, nnz, val, rowptr.device)
+    ws = _workspace(_fn("damn_permute_sym_workspace_size")(n), rowptr.device)
+    dt = _DTYPE_CODE[val.dtype] if val is not None else DAMN_F64
+    rc = _fn("damn_permute_sym")(n, nnz, _ptr(rowptr), _ptr(col), _ptr(val), dt, _ptr(perm),
+                                 _ptr(rp_out), _ptr(col_out), _ptr(val_out), _ptr(ws), ws.numel(),
+                                 _stream(stream))
+    _check(rc, "damn_permute_sym")
+    return rp_out, col_out, val_out
+
+
+def damn_rcm_permute(rowptr, col, val, stream=None):
+    """RCM ordering + P A P^T; returns (perm, rowptr_out, col_out, val_out,
+    {"w_before", "w_after"}).  Synchronises."""
+    n = rowptr.numel() - 1
+    nnz = col.numel()
+    rp_out, col_out, val_out = _perm_outputs(n, nnz, val, rowptr.device)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=rowptr.device)[:n]
+    ws = _workspace(_fn("damn_permute_sym_workspace_size")(n), rowptr.device)
+    info = damn_bw_info()
+    dt = _DTYPE_CODE[val.dtype] if val is not None else DAMN_F64
+    rc = _fn("damn_rcm_permute")(n, nnz, _ptr(rowptr), _ptr(col), _ptr(val), dt, _ptr(perm),
+                                 _ptr(rp_out), _ptr(col_out), _ptr(val_out), ctypes.byref(info),
+                                 _ptr(ws), ws.numel(), _stream(stream))
+    _check(rc, "damn_rcm_permute")
+    return perm, rp_out, col_out, val_out, {"w_before": info.w_before, "w_after": info.w_after}
