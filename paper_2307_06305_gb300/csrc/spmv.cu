@@ -27,6 +27,10 @@ constexpr int kMaxDev = 64;
 constexpr int kRowWeight = 4;       // merge-path weight of a row against an entry
 constexpr int kBalancedItems = 2048;
 constexpr int kXGap = 32;           // columns: smaller gaps are staged, not split
+// every tile's row pointers must fit a stage
+static_assert(kBalancedItems / kRowWeight <= CfgShort::CAP_ROWS, "balanced tiles too tall");
+static_assert(CfgShort::NT <= CfgShort::CAP_ROWS && CfgLong::NT <= CfgLong::CAP_ROWS,
+              "row tiles too tall");
 
 // ----------------------------------------------------------------------------
 // Launch
@@ -80,8 +84,8 @@ int launch_cfg(const SpmvParams &p, cudaStream_t s, int *gs) {
 
 template <typename V, typename I>
 int launch_types(const SpmvParams &p, int shape, cudaStream_t s, int *gs) {
-  if (shape == 1) return launch_cfg<V, I, Cfg128>(p, s, gs);
-  return launch_cfg<V, I, Cfg224>(p, s, gs);
+  if (shape == 1) return launch_cfg<V, I, CfgLong>(p, s, gs);
+  return launch_cfg<V, I, CfgShort>(p, s, gs);
 }
 
 int launch_any(const SpmvParams &p, int dtype, int fmt, int shape, cudaStream_t s, int *gs) {
@@ -122,8 +126,8 @@ __global__ void k_plan_bounds(int nrows, const int *__restrict__ rowptr, long lo
 struct PlanStats {
   unsigned long long sum_group_max;  // sum over 32-row groups of the longest row
   int max_row;
-  int max_tile_short;                // most entries in a Cfg224::NT-row tile
-  int max_tile_long;                 // most entries in a Cfg128::NT-row tile
+  int max_tile_short;                // most entries in a CfgShort::NT-row tile
+  int max_tile_long;                 // most entries in a CfgLong::NT-row tile
   int pad;
 };
 
@@ -137,12 +141,12 @@ __global__ void k_plan_stats(int nrows, const int *__restrict__ rowptr, PlanStat
     atomicAdd(&st->sum_group_max, (unsigned long long)gmax);
     atomicMax(&st->max_row, gmax);
   }
-  if (i < nrows && i % Cfg224::NT == 0) {
-    const int r1 = (int)min((long long)nrows, i + Cfg224::NT);
+  if (i < nrows && i % CfgShort::NT == 0) {
+    const int r1 = (int)min((long long)nrows, i + CfgShort::NT);
     atomicMax(&st->max_tile_short, rowptr[r1] - rowptr[i]);
   }
-  if (i < nrows && i % Cfg128::NT == 0) {
-    const int r1 = (int)min((long long)nrows, i + Cfg128::NT);
+  if (i < nrows && i % CfgLong::NT == 0) {
+    const int r1 = (int)min((long long)nrows, i + CfgLong::NT);
     atomicMax(&st->max_tile_long, rowptr[r1] - rowptr[i]);
   }
 }
@@ -296,7 +300,7 @@ struct damn_plan {
   const void *idx;        // column indices (may be NULL: no x windows)
   int fmt;
   int mode;               // 0 rows per thread, 1 balanced slices
-  int shape;              // 0: Cfg224, 1: Cfg128
+  int shape;              // 0: CfgShort, 1: CfgLong
   int rows_per_tile;      // > 0 fixed row tiles, 0 bounds
   int ntiles;
   int2 *d_bounds;         // bounds of the current tiling (NULL for fixed rows)
@@ -442,8 +446,8 @@ static int plan_xwindows(damn_plan *pl, cudaStream_t s) {
     pl->xseg_cap = pl->ntiles;
   }
   const int asz = pl->dtype == DAMN_F64 ? 8 : 4;
-  const int cap_nz = pl->shape == 1 ? Cfg128::CAP_NZ : Cfg224::CAP_NZ;
-  const int xbytes = pl->shape == 1 ? Cfg128::XBYTES : Cfg224::XBYTES;
+  const int cap_nz = pl->shape == 1 ? CfgLong::CAP_NZ : CfgShort::CAP_NZ;
+  const int xbytes = pl->shape == 1 ? CfgLong::XBYTES : CfgShort::XBYTES;
   const int blocks = std::min(pl->ntiles, 16 * sm_count());
   k_plan_xseg<<<blocks, 256, 0, s>>>(pl->nrows, pl->ncols, pl->rowptr, pl->idx, pl->fmt, pl->ntiles,
                                      pl->rows_per_tile, pl->d_bounds, cap_nz, xbytes / asz,
@@ -473,7 +477,7 @@ static int plan_use(damn_plan *pl, int tiling, cudaStream_t s) {
     const int shape = tiling == DAMN_TILING_ROWS_LONG ? 1 : 0;
     pl->mode = 0;
     pl->shape = shape;
-    pl->rows_per_tile = shape == 1 ? Cfg128::NT : Cfg224::NT;
+    pl->rows_per_tile = shape == 1 ? CfgLong::NT : CfgShort::NT;
     pl->ntiles = (pl->nrows + pl->rows_per_tile - 1) / pl->rows_per_tile;
     pl->d_bounds = nullptr;
   }
@@ -530,9 +534,9 @@ extern "C" int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const
   // Heuristic choice: one row per thread when rows are uniform inside 32-row
   // groups and a row block fits a stage; balanced slices otherwise.
   int tiling = DAMN_TILING_SLICES;
-  if (pl->row_eff >= 0.85 && pl->max_tile_short <= Cfg224::CAP_NZ)
+  if (pl->row_eff >= 0.85 && pl->max_tile_short <= CfgShort::CAP_NZ)
     tiling = DAMN_TILING_ROWS;
-  else if (pl->row_eff >= 0.85 && pl->max_tile_long <= Cfg128::CAP_NZ)
+  else if (pl->row_eff >= 0.85 && pl->max_tile_long <= CfgLong::CAP_NZ)
     tiling = DAMN_TILING_ROWS_LONG;
   int rc = plan_use(pl, tiling, s);
   if (rc) { plan_free_device(pl); delete pl; return rc; }
@@ -595,7 +599,7 @@ extern "C" int damn_plan_describe(const damn_plan *plan, damn_plan_desc *h_desc)
   h_desc->ntiles = plan->ntiles;
   h_desc->grid = plan->grid;
   h_desc->stages = plan->stages;
-  h_desc->threads = plan->shape == 1 ? Cfg128::NT : Cfg224::NT;
+  h_desc->threads = plan->shape == 1 ? CfgLong::NT : CfgShort::NT;
   h_desc->row_efficiency = plan->row_eff;
   h_desc->max_row = plan->max_row;
   h_desc->dtype = plan->dtype;

@@ -71,11 +71,16 @@ struct __align__(16) XSeg {
   int cnt[kXSegMax];
 };
 
-struct TileHdr {
-  int r0, nr, k0, m, rp_sh, v_sh, i_sh, direct;
-  int nseg;
-  int xlo[kXSegMax];   // first column of segment i
-  int xpos[kXSegMax];  // shared-memory slot of column xlo[i]
+// Per-stage tile header written by the producer.  The x-window map is stored
+// ready to use, in tile-local columns cl = c - r0 (see XMap).
+constexpr int kTileDirect = 1;   // entries not staged: read from global memory
+constexpr int kTileStaged = 2;   // x window staged in shared memory
+
+struct __align__(16) TileHdr {
+  int r0, nr, k0, flags;
+  int rp_sh, v_sh, i_sh, d0;
+  int lo1, lo2, lo3, dd1;
+  int dd2, dd3, m, nseg;
 };
 
 struct SpmvParams {
@@ -107,11 +112,15 @@ struct KCfg {
   static constexpr int NT = NT_, CAP_NZ = CAP_NZ_, CAP_ROWS = CAP_ROWS_, XBYTES = XBYTES_;
 };
 
-// 224 consumers (7 warps + producer = 8 warps: two CTAs per SM leave 128
-// registers per thread), stages of 1792 entries: rows of up to ~8 entries.
-// 128 consumers, stages of 3584 entries: rows of up to ~28 entries.
-using Cfg224 = KCfg<224, 1792, 512, 12288>;
-using Cfg128 = KCfg<128, 3584, 128, 12288>;
+// Short rows: 256 consumers (8 warps, two on each SM sub-partition, so the
+// FP64 units of all four carry the same load) + the producer warp, two CTAs
+// per SM (at most 112 registers per thread); row tiles of 256 rows, balanced
+// tiles of up to 512 rows, stages of up to 2048 entries: rows of up to 8
+// entries stay in registers.
+// Long rows: 128 consumers (one warp per sub-partition), stages of 3584
+// entries: rows of up to 28 entries.
+using CfgShort = KCfg<256, 2048, 512, 10240>;
+using CfgLong = KCfg<128, 3584, 128, 12288>;
 
 constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -237,17 +246,25 @@ __device__ __forceinline__ bool issue_tile(const SpmvParams &p, unsigned char *s
     if (rv.tb < mt.k1) load_tail(v_s, val, rv.a0, rv.tb, (long long)mt.k1);
     if (ri.tb < mt.k1) load_tail(i_s, idx, ri.a0, ri.tb, (long long)mt.k1);
   }
-  h.r0 = mt.r0; h.nr = nr; h.k0 = mt.k0; h.m = m; h.direct = direct; h.nseg = nseg;
-  h.rp_sh = static_cast<int>(mt.r0 - rr.a0);
-  h.v_sh = static_cast<int>(mt.k0 - rv.a0);
-  h.i_sh = static_cast<int>(mt.k0 - ri.a0);
+  // x-window map in tile-local columns: segment q starts at column lo_q - r0
+  // and its slot displacement is e_q = pos_q - (lo_q - r0); unused segments
+  // repeat the last displacement and never match (lo = INT_MAX).
+  int e[kXSegMax];
+#pragma unroll
+  for (int q = 0; q < kXSegMax; ++q)
+    e[q] = q < nseg ? mt.pos[q] - (mt.lo[q] - mt.r0) : (q > 0 ? e[q - 1] : 0);
+  const int4 h0 = make_int4(mt.r0, nr, mt.k0, (direct ? kTileDirect : 0) | (nseg > 0 ? kTileStaged : 0));
+  const int4 h1 = make_int4(static_cast<int>(mt.r0 - rr.a0), static_cast<int>(mt.k0 - rv.a0),
+                            static_cast<int>(mt.k0 - ri.a0), e[0]);
+  const int4 h2 = make_int4(nseg > 1 ? mt.lo[1] - mt.r0 : INT_MAX, nseg > 2 ? mt.lo[2] - mt.r0 : INT_MAX,
+                            nseg > 3 ? mt.lo[3] - mt.r0 : INT_MAX, e[1] - e[0]);
+  const int4 h3 = make_int4(e[2] - e[1], e[3] - e[2], m, nseg);
+  int4 *hv = reinterpret_cast<int4 *>(&h);
+  hv[0] = h0; hv[1] = h1; hv[2] = h2; hv[3] = h3;
   uint32_t bytes = rr.bulk_bytes + rv.bulk_bytes + ri.bulk_bytes;
 #pragma unroll
-  for (int q = 0; q < kXSegMax; ++q) {
-    h.xlo[q] = mt.lo[q];
-    h.xpos[q] = mt.pos[q];
+  for (int q = 0; q < kXSegMax; ++q)
     if (q < nseg) bytes += static_cast<uint32_t>(mt.cnt[q]) * sizeof(A);
-  }
   fence_proxy_async_smem();
   mbar_arrive_expect_tx(&full[s], bytes);
   if (rr.bulk_bytes) bulk_copy_g2s(rp_s, p.rowptr + rr.a0, rr.bulk_bytes, &full[s], pol);
@@ -298,29 +315,22 @@ __device__ __forceinline__ void produce(const SpmvParams &p, unsigned char *smem
 // Consumers
 // ----------------------------------------------------------------------------
 
-// Column -> shared-memory slot of the staged x window: with the (at most four)
-// segments sorted by first column and d_i = xpos_i - xlo_i,
-//   slot(c) = c + d_0 + [c >= xlo_1] (d_1 - d_0) + [c >= xlo_2] (d_2 - d_1) + ...
-// Unused segments have xlo = INT_MAX, so there is no branch and no indexing by
-// a runtime segment number: three compares, selects and adds per entry.
+// Tile-local column cl = c - r0 -> shared-memory slot of the staged x window:
+// with the (at most four) segments sorted by first column and e_i their
+// displacements,
+//   slot(cl) = cl + e_0 + [cl >= lo_1] (e_1 - e_0) + [cl >= lo_2] (e_2 - e_1) + ...
+// Unused segments have lo = INT_MAX: no branch and no indexing by a runtime
+// segment number.  For DA-CSR the tile-local column of row r0 + i is simply
+// i + off.
 struct XMap {
   int d0, lo1, lo2, lo3, dd1, dd2, dd3;
   __device__ __forceinline__ void load(const TileHdr &h) {
-    const int n = h.nseg;
-    const int e0 = h.xpos[0] - h.xlo[0];
-    const int e1 = n > 1 ? h.xpos[1] - h.xlo[1] : e0;
-    const int e2 = n > 2 ? h.xpos[2] - h.xlo[2] : e1;
-    const int e3 = n > 3 ? h.xpos[3] - h.xlo[3] : e2;
-    d0 = e0;
-    lo1 = n > 1 ? h.xlo[1] : INT_MAX;
-    lo2 = n > 2 ? h.xlo[2] : INT_MAX;
-    lo3 = n > 3 ? h.xlo[3] : INT_MAX;
-    dd1 = e1 - e0;
-    dd2 = e2 - e1;
-    dd3 = e3 - e2;
+    const int4 *hv = reinterpret_cast<const int4 *>(&h);
+    const int4 b = hv[1], c = hv[2], d = hv[3];
+    d0 = b.w; lo1 = c.x; lo2 = c.y; lo3 = c.z; dd1 = c.w; dd2 = d.x; dd3 = d.y;
   }
-  __device__ __forceinline__ int slot(int c) const {
-    return c + d0 + (c >= lo1 ? dd1 : 0) + (c >= lo2 ? dd2 : 0) + (c >= lo3 ? dd3 : 0);
+  __device__ __forceinline__ int slot(int cl) const {
+    return cl + d0 + (cl >= lo1 ? dd1 : 0) + (cl >= lo2 ? dd2 : 0) + (cl >= lo3 ? dd3 : 0);
   }
 };
 
@@ -362,137 +372,116 @@ struct TileView {
     using L = Layout<V, I, C>;
     unsigned char *st = smem + (size_t)s * L::STAGE;
     rp = reinterpret_cast<const int *>(st) + h.rp_sh;
-    vs = h.direct ? static_cast<const V *>(p.val) + h.k0 : reinterpret_cast<const V *>(st + L::OFF_V) + h.v_sh;
-    is = h.direct ? static_cast<const I *>(p.idx) + h.k0 : reinterpret_cast<const I *>(st + L::OFF_I) + h.i_sh;
+    const bool direct = (h.flags & kTileDirect) != 0;
+    vs = direct ? static_cast<const V *>(p.val) + h.k0 : reinterpret_cast<const V *>(st + L::OFF_V) + h.v_sh;
+    is = direct ? static_cast<const I *>(p.idx) + h.k0 : reinterpret_cast<const I *>(st + L::OFF_I) + h.i_sh;
     xs = reinterpret_cast<const A *>(st + L::OFF_X);
   }
 };
 
-// x value of column c: from the staged window or gathered from global memory.
+// x value of column c of a tile starting at row r0: from the staged window or
+// gathered from global memory.
 template <typename A>
-__device__ __forceinline__ A x_at(const A *xg, const A *xs, const XMap &xm, bool staged, int c) {
-  return staged ? xs[xm.slot(c)] : ldg(xg + c);
+__device__ __forceinline__ A x_at(const A *xg, const A *xs, const XMap &xm, bool staged, int c,
+                                  int r0) {
+  return staged ? xs[xm.slot(c - r0)] : ldg(xg + c);
 }
 
 // Mode 0 -------------------------------------------------------------------
-template <typename V, typename I>
-struct RowWork {
-  using A = typename AccOf<V>::type;
-  static constexpr int U = 8;
-  A av[U], xv[U];
-  int row, cnt;      // row (-1: none); number of entries of the row
-  int s;             // stage the tile came from
-  bool released;     // stage already handed back to the producer
-};
-
-template <typename V, typename I, class C>
-__device__ __forceinline__ bool fetch_rows(const SpmvParams &p, unsigned char *smem,
-                                           uint64_t *full, uint64_t *empty, const TileHdr *hdr,
-                                           int j, int ctid, RowWork<V, I> &w) {
+// A tile that is not fully staged (entries too many for a stage, or no x
+// window): thread i computes rows i, i + NT, ... of the tile, reading what is
+// not in shared memory from global memory.
+template <bool PLAIN, typename V, typename I, class C>
+__device__ __noinline__ void rows_general(const SpmvParams &p, unsigned char *smem,
+                                          const TileHdr &h, int s, int ctid, double &dsum) {
   using A = typename AccOf<V>::type;
   constexpr bool DA = sizeof(I) == 2;
-  constexpr int U = RowWork<V, I>::U;
-  const int s = j % p.stages;
-  if (!mbar_wait_bounded(&full[s], (j / p.stages) & 1, p.status, p.timeout_ns)) return false;
-  const TileHdr &h = hdr[s];
-  const int nr = h.nr, k0 = h.k0, r0 = h.r0;
-  const bool direct = h.direct != 0;
-  const bool staged = h.nseg > 0;
   TileView<V, I, C> tv;
   tv.init(p, smem, h, s);
   XMap xm;
+  const bool staged = (h.flags & kTileStaged) != 0;
   if (staged) xm.load(h);
   const A *xg = static_cast<const A *>(p.x);
-  w.s = s;
-  w.row = -1;
-  w.cnt = 0;
-  if (ctid < nr) {
-    w.row = r0 + ctid;
-    const int b = tv.rp[ctid] - k0;
-    w.cnt = tv.rp[ctid + 1] - k0 - b;
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (u < w.cnt) {
-        const int c = static_cast<int>(tv.is[b + u]) + (DA ? w.row : 0);
-        w.av[u] = to_acc(tv.vs[b + u]);
-        w.xv[u] = x_at(xg, tv.xs, xm, staged, c);
-      }
-    }
-  }
-  // Every row of this warp now in registers: hand the stage back at once (the
-  // arrive orders the shared-memory reads above before it).
-  w.released = false;
-  if (!direct && nr <= C::NT && __all_sync(0xffffffffu, w.cnt <= U)) {
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);
-    w.released = true;
-  }
-  return true;
-}
-
-template <bool PLAIN, typename V, typename I, class C>
-__device__ __forceinline__ void finish_rows(const SpmvParams &p, unsigned char *smem,
-                                            uint64_t *empty, const TileHdr *hdr, int ctid,
-                                            RowWork<V, I> &w, double &dsum) {
-  using A = typename AccOf<V>::type;
-  constexpr bool DA = sizeof(I) == 2;
-  constexpr int U = RowWork<V, I>::U;
-  if (w.row >= 0) {
+  for (int lr = ctid; lr < h.nr; lr += C::NT) {
+    const int row = h.r0 + lr;
     A acc = 0;
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (u < w.cnt) acc = fma_acc(w.av[u], w.xv[u], acc);
-    if (w.cnt > U) {  // long row: the stage is still held, finish from it
-      const TileHdr &h = hdr[w.s];
-      TileView<V, I, C> tv;
-      tv.init(p, smem, h, w.s);
-      XMap xm;
-      const bool staged = h.nseg > 0;
-      if (staged) xm.load(h);
-      const A *xg = static_cast<const A *>(p.x);
-      const int b = tv.rp[ctid] - h.k0;
-      for (int q = b + U; q < b + w.cnt; ++q)
-        acc = fma_acc(to_acc(tv.vs[q]),
-                      x_at(xg, tv.xs, xm, staged, static_cast<int>(tv.is[q]) + (DA ? w.row : 0)),
-                      acc);
-    }
-    store_row<PLAIN>(p, w.row, acc, dsum);
-  }
-  if (!w.released) {
-    const TileHdr &h = hdr[w.s];
-    if (h.nr > C::NT) {  // rows beyond the first NT (not produced by mode-0 plans)
-      TileView<V, I, C> tv;
-      tv.init(p, smem, h, w.s);
-      XMap xm;
-      const bool staged = h.nseg > 0;
-      if (staged) xm.load(h);
-      const A *xg = static_cast<const A *>(p.x);
-      for (int lr = ctid + C::NT; lr < h.nr; lr += C::NT) {
-        const int row = h.r0 + lr;
-        A acc = 0;
-        for (int q = tv.rp[lr] - h.k0; q < tv.rp[lr + 1] - h.k0; ++q)
-          acc = fma_acc(to_acc(tv.vs[q]),
-                        x_at(xg, tv.xs, xm, staged, static_cast<int>(tv.is[q]) + (DA ? row : 0)),
-                        acc);
-        store_row<PLAIN>(p, row, acc, dsum);
-      }
-    }
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[w.s]);
+    for (int q = tv.rp[lr] - h.k0; q < tv.rp[lr + 1] - h.k0; ++q)
+      acc = fma_acc(to_acc(tv.vs[q]),
+                    x_at(xg, tv.xs, xm, staged, static_cast<int>(tv.is[q]) + (DA ? row : 0), h.r0),
+                    acc);
+    store_row<PLAIN>(p, row, acc, dsum);
   }
 }
 
+// One row per thread.  For a fully staged tile (the common case) every
+// operand comes from shared memory through shared-memory pointers: the warp
+// loads its rows' values and x into registers, hands the stage back, then
+// runs the FMA chains, so the warps of a CTA do not wait for each other.
+// Rows longer than U entries finish from the stage before it is released.
 template <bool PLAIN, typename V, typename I, class C>
 __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char *smem,
                                              uint64_t *full, uint64_t *empty, const TileHdr *hdr,
                                              int ctid, double &dsum) {
-  // Each warp loads its rows of a tile into registers, hands the stage back,
-  // then runs the FMA chains; the warps do not wait for each other.
-  RowWork<V, I> w;
+  using L = Layout<V, I, C>;
+  using A = typename AccOf<V>::type;
+  constexpr bool DA = sizeof(I) == 2;
+  constexpr int U = C::CAP_NZ / C::NT;
+  const int lane = threadIdx.x & 31;
   int j = 0;
   for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++j) {
-    if (!fetch_rows<V, I, C>(p, smem, full, empty, hdr, j, ctid, w)) return;
-    finish_rows<PLAIN, V, I, C>(p, smem, empty, hdr, ctid, w, dsum);
+    const int s = j % p.stages;
+    if (!mbar_wait_bounded(&full[s], (j / p.stages) & 1, p.status, p.timeout_ns)) return;
+    const int4 *hv = reinterpret_cast<const int4 *>(&hdr[s]);
+    const int4 h0 = hv[0];  // r0, nr, k0, flags
+    if (h0.w != kTileStaged) {
+      rows_general<PLAIN, V, I, C>(p, smem, hdr[s], s, ctid, dsum);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      continue;
+    }
+    const int4 h1 = hv[1];  // rp_sh, v_sh, i_sh, d0
+    XMap xm;
+    xm.load(hdr[s]);
+    unsigned char *st = smem + (size_t)s * L::STAGE;
+    const int *rp = reinterpret_cast<const int *>(st) + h1.x;
+    const V *vs = reinterpret_cast<const V *>(st + L::OFF_V) + h1.y;
+    const I *is = reinterpret_cast<const I *>(st + L::OFF_I) + h1.z;
+    const A *xs = reinterpret_cast<const A *>(st + L::OFF_X);
+    const int r0 = h0.x, nr = h0.y, k0 = h0.z;
+    A av[U], xv[U];
+    int b = 0, cnt = 0;
+    if (ctid < nr) {
+      b = rp[ctid] - k0;
+      cnt = rp[ctid + 1] - k0 - b;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (u < cnt) {
+          const int cl = DA ? ctid + static_cast<int>(is[b + u]) : static_cast<int>(is[b + u]) - r0;
+          av[u] = to_acc(vs[b + u]);
+          xv[u] = xs[xm.slot(cl)];
+        }
+      }
+    }
+    const bool fits = __all_sync(0xffffffffu, cnt <= U);
+    if (fits) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
+    if (ctid < nr) {
+      A acc = 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (u < cnt) acc = fma_acc(av[u], xv[u], acc);
+      for (int q = b + U; q < b + cnt; ++q) {  // only when !fits
+        const int cl = DA ? ctid + static_cast<int>(is[q]) : static_cast<int>(is[q]) - r0;
+        acc = fma_acc(to_acc(vs[q]), xs[xm.slot(cl)], acc);
+      }
+      store_row<PLAIN>(p, r0 + ctid, acc, dsum);
+    }
+    if (!fits) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
   }
 }
 
@@ -508,7 +497,7 @@ __device__ __forceinline__ void tile_slices(const SpmvParams &p, const TileHdr &
   const A *xg = static_cast<const A *>(p.x);
   const int *rp = tv.rp;
   const int nr = h.nr, m = h.m, k0 = h.k0;
-  const bool staged = h.nseg > 0;
+  const bool staged = (h.flags & kTileStaged) != 0;
   XMap xm;
   if (staged) xm.load(h);
   const int K = m > 0 ? (m + C::NT - 1) / C::NT : 0;
@@ -537,7 +526,7 @@ __device__ __forceinline__ void tile_slices(const SpmvParams &p, const TileHdr &
           while (tend <= q + u) { ++tcr; tend = rp[tcr + 1] - k0; }
           const int c = static_cast<int>(tv.is[q + u]) + (DA ? h.r0 + tcr : 0);
           av[u] = to_acc(tv.vs[q + u]);
-          xv[u] = x_at(xg, tv.xs, xm, staged, c);
+          xv[u] = x_at(xg, tv.xs, xm, staged, c, h.r0);
         }
       }
 #pragma unroll
