@@ -16,6 +16,20 @@ roofline of the SpMV kernel against the measured HBM copy bandwidth, GPU
 clocks sampled during the timed region, and the plain-C oracle (Listing 2)
 timed on the host cores as a CPU baseline.
 
+Secondary sections of the same line (each on its own synthetic workload,
+none of them inside the headline's timed region):
+  * ``conversion`` / ``rcm``: CSR -> DA-CSR-16 throughput; the 128^3 grid
+    under a seeded random symmetric permutation (int16 fit rate), RCM on it
+    (host ordering + device P A P^T) and SpMV throughput after RCM;
+  * ``solvers``: 160^3 27-point stencil, time to a true relative residual of
+    1e-10 for FP64 CG and for CG with FP64 refinement around FP32 / BF16
+    DA-CSR-16 inner solves;
+  * ``batched``: 512 random banded matrices, k in {1, 4, 16} right-hand
+    sides, FP64 / FP32: one persistent launch (direct and graph replay) vs
+    512 per-matrix launches (eager and graph-captured);
+  * ``small``: the 64x64 5-point Laplacian, SpMV time per call under graph
+    replay (launch / latency bound, in L2).
+
 ``--impl reference`` times the oracle (the plain-C Listing 2 restatement)
 on the host cores instead, for the same metric and workload.
 
@@ -186,6 +200,243 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# secondary sections
+# ----------------------------------------------------------------------------
+
+def _event_time(torch, fn, reps, stream=None):
+    """Median and min seconds of fn() over reps, CUDA events on the stream."""
+    stream = stream or torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    return statistics.median(ts), min(ts)
+
+
+def section_conversion_rcm(D, torch, dev, reps):
+    """a1 conversion throughput on the natural 128^3 grid; a2 RCM on its
+    seeded random symmetric permutation; SpMV after RCM."""
+    import workloads as W
+    out = {}
+    rp, col, val = W.laplace3d_7pt(GRID)
+    n, nnz = len(rp) - 1, len(col)
+    t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
+    off = torch.empty(nnz, dtype=torch.int16, device=dev)
+    D.damn_csr_to_dacsr(t_rp, t_col, n, off_out=off)
+    med, mn = _event_time(torch, lambda: D.damn_csr_to_dacsr(t_rp, t_col, n, off_out=off), reps)
+    b = (n + 1) * 4 + nnz * (4 + 2)
+    out["conversion"] = {"workload": "laplace3d_7pt_128^3_natural", "us": round(med * 1e6, 1),
+                         "gbs": round(b / med / 1e9, 1), "bytes": b,
+                         "note": "includes the synchronising fit-info read-back"}
+    del t_col, off
+    rp, col, val = W.laplace3d_7pt(GRID, scrambled=True, rng=W.rng_for(2, 1))
+    t_rp, t_col, t_val = (torch.from_numpy(a).to(dev) for a in (rp, col, val))
+    _, fi = D.damn_csr_to_dacsr(t_rp, t_col, n)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    perm, rp2, col2, val2, bw = D.damn_rcm_permute(t_rp, t_col, t_val)
+    t_rcm = time.perf_counter() - t0
+    off2, fi2 = D.damn_csr_to_dacsr(rp2, col2, n, raise_on_nofit=True)
+    med_p, _ = _event_time(torch, lambda: D.damn_permute_sym(t_rp, t_col, t_val, perm), reps)
+    # SpMV after RCM, NCOPY rotating copies (> L2)
+    cp = [(rp2, off2, col2, val2)] + [(rp2.clone(), off2.clone(), col2.clone(), val2.clone())
+                                     for _ in range(NCOPY - 1)]
+    x = torch.from_numpy(W.uniform_vector(n, W.rng_for(2, 0))).to(dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    plans = [D.Plan(c[0], nnz, n, torch.float64, idx=c[1]) for c in cp]
+    plans[0].autotune(D.DAMN_FMT_DACSR16, cp[0][1], cp[0][3], x, y)
+    for p_ in plans[1:]:
+        p_.set_tiling(plans[0].describe()["tiling"])
+    it = [0]
+
+    def da():
+        c = it[0] % NCOPY
+        it[0] += 1
+        D.damn_spmv_dacsr16(cp[c][0], cp[c][1], cp[c][3], x, y, plan=plans[c])
+
+    def cs():
+        c = it[0] % NCOPY
+        it[0] += 1
+        D.damn_spmv_csr32(cp[c][0], cp[c][2], cp[c][3], x, y, plan=plans[c])
+    for _ in range(8):
+        da()
+        cs()
+    t_da, _ = _event_time(torch, lambda: [da() for _ in range(40)], 5)
+    t_cs, _ = _event_time(torch, lambda: [cs() for _ in range(40)], 5)
+    t_da, t_cs = t_da / 40, t_cs / 40
+    out["rcm"] = {
+        "workload": "laplace3d_7pt_128^3_random_symmetric_permutation",
+        "fit_rate_scrambled": round(fi.n_fit / nnz, 4), "fits_scrambled": bool(fi.fits),
+        "w_scrambled": bw["w_before"], "w_after_rcm": bw["w_after"],
+        "fit_rate_after_rcm": round(fi2.n_fit / nnz, 4),
+        "rcm_permute_s": round(t_rcm, 3), "permute_sym_ms": round(med_p * 1e3, 3),
+        "spmv_after_rcm": {"da16_gbs": round(spmv_bytes(n, nnz, 2, 8, 8) / t_da / 1e9, 1),
+                           "csr32_gbs": round(spmv_bytes(n, nnz, 4, 8, 8) / t_cs / 1e9, 1),
+                           "da16_us": round(t_da * 1e6, 2), "csr32_us": round(t_cs * 1e6, 2),
+                           "speedup_da16_over_csr32": round(t_cs / t_da, 4),
+                           "tiling": plans[0].describe()["tiling"]}}
+    return out
+
+
+def section_solvers(D, torch, dev, reps):
+    """a5/a6: FP64 CG vs CG-IR (FP32 / BF16 inner values) on the 160^3
+    27-point stencil, time to a true relative residual of 1e-10."""
+    import workloads as W
+    m = 160
+    rp, col, val = W.stencil27(m)
+    n, nnz = len(rp) - 1, len(col)
+    t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
+    off, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
+    del t_col
+    t_val = torch.from_numpy(val).to(dev)
+    del rp, col, val
+    v32 = D.damn_cast_values(t_val, torch.float32)
+    v16 = D.damn_cast_values(t_val, torch.bfloat16)
+    xs = torch.from_numpy(W.uniform_vector(n, W.rng_for(4, 1))).to(dev)
+    b = torch.empty(n, dtype=torch.float64, device=dev)
+    D.damn_spmv_dacsr16(t_rp, off, t_val, xs, b)                 # b = A x*
+    p64 = D.Plan(t_rp, nnz, n, torch.float64, idx=off)
+    p32 = D.Plan(t_rp, nnz, n, torch.float32, idx=off)
+    p16 = D.Plan(t_rp, nnz, n, torch.bfloat16, idx=off)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    p64.autotune(D.DAMN_FMT_DACSR16, off, t_val, xs, y)
+    x32, y32 = xs.float(), torch.empty(n, dtype=torch.float32, device=dev)
+    p32.autotune(D.DAMN_FMT_DACSR16, off, v32, x32, y32)
+    p16.autotune(D.DAMN_FMT_DACSR16, off, v16, x32, y32)
+    ws_cg = D._workspace(D._fn("damn_cg_workspace_size")(n), dev)
+    ws_ir = D._workspace(D._fn("damn_cg_ir_workspace_size")(n), dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    runs = {
+        "cg_f64": lambda: D.damn_cg(t_rp, off, t_val, b, x, 1e-10, 2000, plan=p64, workspace=ws_cg),
+        "cg_ir_f32": lambda: D.damn_cg_ir(t_rp, off, t_val, v32, b, x, 1e-10, 1e-3, 200, 60,
+                                          plan64=p64, plan_low=p32, workspace=ws_ir),
+        "cg_ir_bf16": lambda: D.damn_cg_ir(t_rp, off, t_val, v16, b, x, 1e-10, 1e-2, 200, 60,
+                                           plan64=p64, plan_low=p16, workspace=ws_ir),
+    }
+    out = {"workload": "stencil27_160^3_cg_to_1e-10", "n": n, "nnz": nnz}
+    stream = torch.cuda.current_stream()
+    for name, fn in runs.items():
+        ts, res = [], None
+        for r in range(reps + 1):
+            x.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            e1.synchronize()
+            if r > 0:                                            # first run warms up
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+        err = float(torch.linalg.vector_norm(x - xs) / torch.linalg.vector_norm(xs))
+        out[name] = {"ms": round(statistics.median(ts) * 1e3, 2),
+                     "ms_min": round(min(ts) * 1e3, 2),
+                     "iterations": res["iterations"], "outer": res.get("outer", 0),
+                     "converged": bool(res["converged"]),
+                     "true_relres": float(f"{res['true_relres']:.3e}"),
+                     "rel_err_vs_xstar": float(f"{err:.3e}")}
+    for name in ("cg_ir_f32", "cg_ir_bf16"):
+        out[name]["speedup_vs_cg_f64"] = round(out["cg_f64"]["ms"] / out[name]["ms"], 3)
+    return out
+
+
+def section_batched(D, torch, dev, reps):
+    """a7: 512 independent banded matrices, k in {1, 4, 16}, FP64 / FP32."""
+    import workloads as W
+    mats_np = W.batch_banded(512)
+    out = {"workload": "batch_banded_512", "count": len(mats_np),
+           "rows": int(sum(m[0] for m in mats_np)), "nnz": int(sum(len(m[2]) for m in mats_np))}
+    base = []
+    for n, rp, col, val in mats_np:
+        t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
+        off, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
+        base.append((n, t_rp, off, torch.from_numpy(val).to(dev)))
+    del mats_np
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.seed_for(5, 1))
+    stream = torch.cuda.current_stream()
+    for dt, s in ((torch.float64, 8), (torch.float32, 4)):
+        vals = [v.to(dt) for (_, _, _, v) in base]
+        for k in (1, 4, 16):
+            mats = []
+            for (n, t_rp, off, _), v in zip(base, vals):
+                X = torch.rand((n, k), generator=gen, device=dev, dtype=dt) * 2 - 1
+                Y = torch.empty((n, k), dtype=dt, device=dev)
+                mats.append((t_rp, off, v, X, Y))
+            nbytes = sum((m[0].numel()) * 4 + m[1].numel() * (2 + s) + 2 * m[3].numel() * s
+                         for m in mats)
+            flops = sum(2 * m[1].numel() * k for m in mats)
+            plan = D.BatchPlan(mats, k, dt, autotune=True)
+            t_b, _ = _event_time(torch, plan.launch, reps)
+            t_g, _ = _event_time(torch, plan.graph_launch, reps)
+
+            def per_matrix():
+                for (rp_, off_, v_, X_, Y_) in mats:
+                    D.damn_spmm_dacsr16(rp_, off_, v_, X_, Y_)
+            per_matrix()
+            t_e, _ = _event_time(torch, per_matrix, reps)
+            g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                per_matrix()
+            stream.wait_stream(side)
+            with torch.cuda.graph(g):
+                per_matrix()
+            g.replay()
+            t_pg, _ = _event_time(torch, g.replay, reps)
+            desc = plan.describe()
+            key = f"{'f64' if s == 8 else 'f32'}_k{k}"
+            out[key] = {"batched_graph_gbs": round(nbytes / t_g / 1e9, 1),
+                        "batched_graph_ms": round(t_g * 1e3, 3),
+                        "batched_direct_ms": round(t_b * 1e3, 3),
+                        "per_matrix_eager_ms": round(t_e * 1e3, 3),
+                        "per_matrix_graph_ms": round(t_pg * 1e3, 3),
+                        "speedup_vs_per_matrix_graph": round(t_pg / t_g, 3),
+                        "gflops": round(flops / t_g / 1e9, 1), "bytes": nbytes,
+                        "tuned": {"rows_per_item": desc["tile_items"], "threads": desc["threads"],
+                                  "grid": desc["grid"]}}
+            plan.close()
+            del g, mats, plan
+        del vals
+    return out
+
+
+def section_small(D, torch, dev, reps):
+    """Config 1 size (64x64 5-point Laplacian, in L2): time per SpMV under
+    graph replay of 1000 calls."""
+    import workloads as W
+    rp, col, val = W.laplace2d_5pt(64)
+    n, nnz = len(rp) - 1, len(col)
+    t_rp, t_col, t_val = (torch.from_numpy(a).to(dev) for a in (rp, col, val))
+    off, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
+    x = torch.from_numpy(W.uniform_vector(n, W.rng_for(1, 0))).to(dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    plan = D.Plan(t_rp, nnz, n, torch.float64, idx=off)
+    out = {"workload": "laplace2d_5pt_64^2", "n": n, "nnz": nnz}
+    for name, call in (("da16", lambda: D.damn_spmv_dacsr16(t_rp, off, t_val, x, y, plan=plan)),
+                       ("csr32", lambda: D.damn_spmv_csr32(t_rp, t_col, t_val, x, y, plan=plan))):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            call()
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(1000):
+                call()
+        g.replay()
+        t, _ = _event_time(torch, g.replay, reps)
+        out[f"{name}_us_per_spmv"] = round(t / 1000 * 1e6, 3)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,6 +444,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--sections", default="conversion,solvers,batched,small",
+                    help="comma list of secondary sections to run after the headline ('' for none)")
+    ap.add_argument("--section-reps", type=int, default=10)
+    ap.add_argument("--tiling", default="auto", choices=["auto", "rows", "rows_long", "slices"],
+                    help="headline plan tiling: autotuned, or fixed")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -225,8 +481,13 @@ def main():
     t_x = torch.from_numpy(x).to(dev)
     y = torch.empty(n, dtype=torch.float64, device=dev)
     plans = [D.Plan(t_rp[c], nnz, n, torch.float64, idx=t_off[c]) for c in range(NCOPY)]
-    plans[0].autotune(D.DAMN_FMT_DACSR16, t_off[0], t_val[0], t_x, y)
-    tiling = plans[0].describe()["tiling"]
+    if args.tiling == "auto":
+        plans[0].autotune(D.DAMN_FMT_DACSR16, t_off[0], t_val[0], t_x, y)
+        tiling = plans[0].describe()["tiling"]
+    else:
+        tiling = {"rows": D.DAMN_TILING_ROWS, "rows_long": D.DAMN_TILING_ROWS_LONG,
+                  "slices": D.DAMN_TILING_SLICES}[args.tiling]
+        plans[0].set_tiling(tiling)
     for c in range(1, NCOPY):
         plans[c].set_tiling(tiling)
     stream = torch.cuda.current_stream()
@@ -338,6 +599,17 @@ def main():
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
+    secs = [t for t in args.sections.split(",") if t]
+    fns = {"conversion": section_conversion_rcm, "solvers": section_solvers,
+           "batched": section_batched, "small": section_small}
+    for name in secs:
+        t0 = time.perf_counter()
+        res = fns[name](D, torch, dev, args.section_reps)
+        line.setdefault("sections", {}).update(res if name == "conversion" else {name: res})
+        line["sections"].setdefault("_seconds", {})[name] = round(time.perf_counter() - t0, 1)
+        torch.cuda.empty_cache()
+    if D.damn_device_status() != 0:
+        raise RuntimeError("device status word reports an error after the sections")
     if rank == 0:
         from oracle import dacsr as OD
         t_cpu, reps, cores = cpu_oracle_baseline(rp, OD.translate(n, rp, col).astype(np.int16),

@@ -265,7 +265,9 @@ __device__ __forceinline__ bool issue_tile(const SpmvParams &p, unsigned char *s
 #pragma unroll
   for (int q = 0; q < kXSegMax; ++q)
     if (q < nseg) bytes += static_cast<uint32_t>(mt.cnt[q]) * sizeof(A);
-  fence_proxy_async_smem();
+  // No proxy fence: the async copies write only bytes that no generic store
+  // of this tile writes, and the consumers' reads of the stage's previous
+  // tile are ordered before these copies by the empty barrier.
   mbar_arrive_expect_tx(&full[s], bytes);
   if (rr.bulk_bytes) bulk_copy_g2s(rp_s, p.rowptr + rr.a0, rr.bulk_bytes, &full[s], pol);
   if (rv.bulk_bytes) bulk_copy_g2s(v_s, val + rv.a0, rv.bulk_bytes, &full[s], pol);

@@ -145,7 +145,7 @@ def test_rcm_permute_full_size_scrambled_128(D, cuda_dev):
     bandwidths match Eq. (2), and B fits DA-CSR-16."""
     m = 128
     n = m ** 3
-    rp, c, v = W.laplace3d_7pt(m, scrambled=True, rng=W.rng_for(3))
+    rp, c, v = W.laplace3d_7pt(m, scrambled=True, rng=W.rng_for(2, 1))
     t = lambda a: torch.from_numpy(a).to(cuda_dev)
     perm, rp_o, col_o, val_o, info = D.damn_rcm_permute(t(rp), t(c), t(v))
     p = perm.cpu().numpy()

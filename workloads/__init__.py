@@ -218,7 +218,11 @@ def _banded_rows(n: int, h_lo, h_hi, k: np.ndarray, rng: np.random.Generator,
     draw = rng.integers(0, width[rr])
     cols = np.concatenate([lo[rr] + draw, r])
     rows = np.concatenate([rr, np.arange(nr, dtype=np.int64)])
-    key = np.unique(rows * n + cols)
+    key = rows * n + cols
+    key.sort()
+    keep = np.ones(len(key), dtype=bool)
+    np.not_equal(key[1:], key[:-1], out=keep[1:])
+    key = key[keep]                      # sorted, duplicates removed
     rows_u = key // n
     cols_u = key - rows_u * n
     counts = np.bincount(rows_u, minlength=nr)
