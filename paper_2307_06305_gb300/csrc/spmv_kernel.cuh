@@ -213,11 +213,68 @@ __device__ __forceinline__ void load_tail(T *dst, const T *src, long long a0, lo
   for (long long e = tb; e < end; ++e) dst[e - a0] = src[e];
 }
 
-// Issues one tile into stage s (one lane).  Returns false when the wait for a
-// free stage gave up.
+// Everything the producer needs to issue one tile, computed ahead (by the
+// lane that will issue it, 32 tiles at a time in parallel): the stage
+// header, the 16-byte aligned bulk ranges of row pointers / values /
+// indices, the x segments, and whether a partial block at the very end of an
+// array has to be loaded with plain loads.
+struct TileIssue {
+  int4 h0, h1, h2, h3;       // stage header (TileHdr layout)
+  long long rp_a0, v_a0, i_a0;
+  uint32_t rp_bytes, v_bytes, i_bytes, tx_bytes;
+  int xsrc[kXSegMax], xdst[kXSegMax], xcnt[kXSegMax];
+  int tails;                 // a plain-loaded tail exists (last tiles only)
+};
+
+template <typename V, typename I, class C>
+__device__ __forceinline__ void prepare_tile(const SpmvParams &p, long long t, TileIssue &ti) {
+  using A = typename AccOf<V>::type;
+  TileMeta mt;
+  load_meta<C>(p, t, mt);
+  const int nr = mt.r1 - mt.r0, m = mt.k1 - mt.k0;
+  const int direct = m > C::CAP_NZ ? 1 : 0;
+  const int nseg = direct ? 0 : mt.nseg;
+  const Range rr = split_range<4>(mt.r0, nr + 1, (long long)p.nrows + 1);
+  Range rv{mt.k0, mt.k0, 0u}, ri{mt.k0, mt.k0, 0u};
+  if (!direct && m > 0) {
+    rv = split_range<(int)sizeof(V)>(mt.k0, m, p.nnz);
+    ri = split_range<(int)sizeof(I)>(mt.k0, m, p.nnz);
+  }
+  ti.tails = (rr.tb < mt.r1 + 1) || (!direct && m > 0 && (rv.tb < mt.k1 || ri.tb < mt.k1));
+  // x-window map in tile-local columns: segment q starts at column lo_q - r0
+  // and its slot displacement is e_q = pos_q - (lo_q - r0); unused segments
+  // repeat the last displacement and never match (lo = INT_MAX).
+  int e[kXSegMax];
+#pragma unroll
+  for (int q = 0; q < kXSegMax; ++q)
+    e[q] = q < nseg ? mt.pos[q] - (mt.lo[q] - mt.r0) : (q > 0 ? e[q - 1] : 0);
+  ti.h0 = make_int4(mt.r0, nr, mt.k0, (direct ? kTileDirect : 0) | (nseg > 0 ? kTileStaged : 0));
+  ti.h1 = make_int4(static_cast<int>(mt.r0 - rr.a0), static_cast<int>(mt.k0 - rv.a0),
+                    static_cast<int>(mt.k0 - ri.a0), e[0]);
+  ti.h2 = make_int4(nseg > 1 ? mt.lo[1] - mt.r0 : INT_MAX, nseg > 2 ? mt.lo[2] - mt.r0 : INT_MAX,
+                    nseg > 3 ? mt.lo[3] - mt.r0 : INT_MAX, e[1] - e[0]);
+  ti.h3 = make_int4(e[2] - e[1], e[3] - e[2], m, nseg);
+  ti.rp_a0 = rr.a0; ti.rp_bytes = rr.bulk_bytes;
+  ti.v_a0 = rv.a0; ti.v_bytes = rv.bulk_bytes;
+  ti.i_a0 = ri.a0; ti.i_bytes = ri.bulk_bytes;
+  uint32_t bytes = rr.bulk_bytes + rv.bulk_bytes + ri.bulk_bytes;
+#pragma unroll
+  for (int q = 0; q < kXSegMax; ++q) {
+    const bool on = q < nseg && mt.cnt[q] > 0;
+    ti.xsrc[q] = mt.src[q];
+    ti.xdst[q] = mt.pos[q] - (mt.lo[q] - mt.src[q]);
+    ti.xcnt[q] = on ? mt.cnt[q] : 0;
+    bytes += static_cast<uint32_t>(ti.xcnt[q]) * sizeof(A);
+  }
+  ti.tx_bytes = bytes;
+}
+
+// Issues tile j (prepared in ti) into stage j % stages (one lane): wait for
+// the stage, write its header, post the byte count, start the bulk copies.
+// Returns false when the wait for a free stage gave up.
 template <typename V, typename I, class C>
 __device__ __forceinline__ bool issue_tile(const SpmvParams &p, unsigned char *smem, uint64_t *full,
-                                           uint64_t *empty, TileHdr *hdr, const TileMeta &mt,
+                                           uint64_t *empty, TileHdr *hdr, const TileIssue &ti,
                                            int j, uint64_t pol) {
   using L = Layout<V, I, C>;
   using A = typename L::A;
@@ -233,57 +290,38 @@ __device__ __forceinline__ bool issue_tile(const SpmvParams &p, unsigned char *s
   const V *val = static_cast<const V *>(p.val);
   const I *idx = static_cast<const I *>(p.idx);
   const A *x = static_cast<const A *>(p.x);
-  TileHdr &h = hdr[s];
-  const int nr = mt.r1 - mt.r0, m = mt.k1 - mt.k0;
-  const int direct = m > C::CAP_NZ ? 1 : 0;
-  const int nseg = direct ? 0 : mt.nseg;
-  const Range rr = split_range<4>(mt.r0, nr + 1, (long long)p.nrows + 1);
-  if (rr.tb < mt.r1 + 1) load_tail(rp_s, p.rowptr, rr.a0, rr.tb, (long long)mt.r1 + 1);
-  Range rv{mt.k0, mt.k0, 0u}, ri{mt.k0, mt.k0, 0u};
-  if (!direct && m > 0) {
-    rv = split_range<(int)sizeof(V)>(mt.k0, m, p.nnz);
-    ri = split_range<(int)sizeof(I)>(mt.k0, m, p.nnz);
-    if (rv.tb < mt.k1) load_tail(v_s, val, rv.a0, rv.tb, (long long)mt.k1);
-    if (ri.tb < mt.k1) load_tail(i_s, idx, ri.a0, ri.tb, (long long)mt.k1);
+  if (ti.tails) {  // partial 16-byte blocks at the very end of an array
+    const int r0 = ti.h0.x, nr = ti.h0.y, k0 = ti.h0.z, m = ti.h3.z;
+    const long long rtb = ti.rp_a0 + ti.rp_bytes / 4;
+    if (rtb < r0 + nr + 1) load_tail(rp_s, p.rowptr, ti.rp_a0, rtb, (long long)r0 + nr + 1);
+    if (!(ti.h0.w & kTileDirect) && m > 0) {
+      const long long vtb = ti.v_a0 + ti.v_bytes / sizeof(V);
+      const long long itb = ti.i_a0 + ti.i_bytes / sizeof(I);
+      if (vtb < k0 + m) load_tail(v_s, val, ti.v_a0, vtb, (long long)k0 + m);
+      if (itb < k0 + m) load_tail(i_s, idx, ti.i_a0, itb, (long long)k0 + m);
+    }
   }
-  // x-window map in tile-local columns: segment q starts at column lo_q - r0
-  // and its slot displacement is e_q = pos_q - (lo_q - r0); unused segments
-  // repeat the last displacement and never match (lo = INT_MAX).
-  int e[kXSegMax];
-#pragma unroll
-  for (int q = 0; q < kXSegMax; ++q)
-    e[q] = q < nseg ? mt.pos[q] - (mt.lo[q] - mt.r0) : (q > 0 ? e[q - 1] : 0);
-  const int4 h0 = make_int4(mt.r0, nr, mt.k0, (direct ? kTileDirect : 0) | (nseg > 0 ? kTileStaged : 0));
-  const int4 h1 = make_int4(static_cast<int>(mt.r0 - rr.a0), static_cast<int>(mt.k0 - rv.a0),
-                            static_cast<int>(mt.k0 - ri.a0), e[0]);
-  const int4 h2 = make_int4(nseg > 1 ? mt.lo[1] - mt.r0 : INT_MAX, nseg > 2 ? mt.lo[2] - mt.r0 : INT_MAX,
-                            nseg > 3 ? mt.lo[3] - mt.r0 : INT_MAX, e[1] - e[0]);
-  const int4 h3 = make_int4(e[2] - e[1], e[3] - e[2], m, nseg);
-  int4 *hv = reinterpret_cast<int4 *>(&h);
-  hv[0] = h0; hv[1] = h1; hv[2] = h2; hv[3] = h3;
-  uint32_t bytes = rr.bulk_bytes + rv.bulk_bytes + ri.bulk_bytes;
-#pragma unroll
-  for (int q = 0; q < kXSegMax; ++q)
-    if (q < nseg) bytes += static_cast<uint32_t>(mt.cnt[q]) * sizeof(A);
+  int4 *hv = reinterpret_cast<int4 *>(&hdr[s]);
+  hv[0] = ti.h0; hv[1] = ti.h1; hv[2] = ti.h2; hv[3] = ti.h3;
   // No proxy fence: the async copies write only bytes that no generic store
   // of this tile writes, and the consumers' reads of the stage's previous
   // tile are ordered before these copies by the empty barrier.
-  mbar_arrive_expect_tx(&full[s], bytes);
-  if (rr.bulk_bytes) bulk_copy_g2s(rp_s, p.rowptr + rr.a0, rr.bulk_bytes, &full[s], pol);
-  if (rv.bulk_bytes) bulk_copy_g2s(v_s, val + rv.a0, rv.bulk_bytes, &full[s], pol);
-  if (ri.bulk_bytes) bulk_copy_g2s(i_s, idx + ri.a0, ri.bulk_bytes, &full[s], pol);
+  mbar_arrive_expect_tx(&full[s], ti.tx_bytes);
+  if (ti.rp_bytes) bulk_copy_g2s(rp_s, p.rowptr + ti.rp_a0, ti.rp_bytes, &full[s], pol);
+  if (ti.v_bytes) bulk_copy_g2s(v_s, val + ti.v_a0, ti.v_bytes, &full[s], pol);
+  if (ti.i_bytes) bulk_copy_g2s(i_s, idx + ti.i_a0, ti.i_bytes, &full[s], pol);
 #pragma unroll
   for (int q = 0; q < kXSegMax; ++q)
-    if (q < nseg && mt.cnt[q] > 0)
-      bulk_copy_g2s_nohint(x_s + (mt.pos[q] - (mt.lo[q] - mt.src[q])), x + mt.src[q],
-                           static_cast<uint32_t>(mt.cnt[q]) * sizeof(A), &full[s]);
+    if (ti.xcnt[q] > 0)
+      bulk_copy_g2s_nohint(x_s + ti.xdst[q], x + ti.xsrc[q],
+                           static_cast<uint32_t>(ti.xcnt[q]) * sizeof(A), &full[s]);
   return true;
 }
 
 // Producer warp: for each group of 32 consecutive tiles of this CTA, lane i
-// loads the bounds and staging descriptors of tile i (one round of memory
-// latency per 32 tiles, all lanes in parallel); then lane i issues tile i,
-// in tile order.
+// prepares tile i (bounds, staging descriptors, copy ranges, header: one
+// round of memory latency and the arithmetic for 32 tiles, all lanes in
+// parallel); then lane i issues tile i, in tile order.
 template <typename V, typename I, class C>
 __device__ __forceinline__ void produce(const SpmvParams &p, unsigned char *smem, uint64_t *full,
                                         uint64_t *empty, TileHdr *hdr) {
@@ -293,14 +331,14 @@ __device__ __forceinline__ void produce(const SpmvParams &p, unsigned char *smem
   bool stop = false;
   while (!stop) {
     const long long tl = (long long)blockIdx.x + (long long)(j + lane) * gridDim.x;
-    TileMeta mt;
-    if (tl < p.ntiles) load_meta<C>(p, tl, mt);
+    TileIssue ti;
+    if (tl < p.ntiles) prepare_tile<V, I, C>(p, tl, ti);
     const int jl = j + lane;
     for (int i = 0; i < 32; ++i) {
       const long long t = (long long)blockIdx.x + (long long)j * gridDim.x;
       if (t >= p.ntiles) { stop = true; break; }
       int ok = 1;
-      if (lane == i) ok = issue_tile<V, I, C>(p, smem, full, empty, hdr, mt, jl, pol) ? 1 : 0;
+      if (lane == i) ok = issue_tile<V, I, C>(p, smem, full, empty, hdr, ti, jl, pol) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, i);
       if (!ok) { stop = true; break; }
       ++j;
