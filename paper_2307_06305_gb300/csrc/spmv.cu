@@ -28,8 +28,9 @@ constexpr int kRowWeight = 4;       // merge-path weight of a row against an ent
 constexpr int kBalancedItems = 2048;
 constexpr int kXGap = 32;           // columns: smaller gaps are staged, not split
 // every tile's row pointers must fit a stage
-static_assert(kBalancedItems / kRowWeight <= CfgShort::CAP_ROWS, "balanced tiles too tall");
-static_assert(CfgShort::NT <= CfgShort::CAP_ROWS && CfgLong::NT <= CfgLong::CAP_ROWS,
+static_assert(kBalancedItems / kRowWeight <= CfgSlices::CAP_ROWS, "balanced tiles too tall");
+static_assert(CfgShort::NT <= CfgShort::CAP_ROWS && CfgLong::NT <= CfgLong::CAP_ROWS &&
+                  256 <= CfgSlices::CAP_ROWS,
               "row tiles too tall");
 
 // ----------------------------------------------------------------------------
@@ -52,14 +53,14 @@ int launch_kernel(SpmvParams p, cudaStream_t s, int *gs_out) {
       DAMN_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
       DAMN_CUDA(cudaFuncSetAttribute(k_spmv<PLAIN, V, I, C>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin));
-      // deepest ring that keeps two CTAs per SM (at least two stages)
+      // deepest ring that keeps C::MINB CTAs per SM (at least two stages)
       int best_s = 2, best_o = 0;
       for (int st = kMaxStages; st >= 2; --st) {
         if (L::total(st, mode) > (size_t)max_optin) continue;
         int o = 0;
         DAMN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_spmv<PLAIN, V, I, C>,
                                                                 C::NT + 32, L::total(st, mode)));
-        if (o >= 2) { best_s = st; best_o = o; break; }
+        if (o >= C::MINB) { best_s = st; best_o = o; break; }
         if (o > best_o) { best_s = st; best_o = o; }
       }
       stages_of[dev][mode] = best_s;
@@ -85,6 +86,7 @@ int launch_cfg(const SpmvParams &p, cudaStream_t s, int *gs) {
 template <typename V, typename I>
 int launch_types(const SpmvParams &p, int shape, cudaStream_t s, int *gs) {
   if (shape == 1) return launch_cfg<V, I, CfgLong>(p, s, gs);
+  if (shape == 2) return launch_cfg<V, I, CfgSlices>(p, s, gs);
   return launch_cfg<V, I, CfgShort>(p, s, gs);
 }
 
@@ -300,7 +302,7 @@ struct damn_plan {
   const void *idx;        // column indices (may be NULL: no x windows)
   int fmt;
   int mode;               // 0 rows per thread, 1 balanced slices
-  int shape;              // 0: CfgShort, 1: CfgLong
+  int shape;              // kernel configuration: 0 CfgShort, 1 CfgLong, 2 CfgSlices
   int rows_per_tile;      // > 0 fixed row tiles, 0 bounds
   int ntiles;
   int2 *d_bounds;         // bounds of the current tiling (NULL for fixed rows)
@@ -352,7 +354,7 @@ static int make_params(const SpmvCall &c, const damn_plan *plan, SpmvParams &p, 
     p.ntiles = (c.nrows + 255) / 256;
     p.bounds = nullptr;
     p.xseg = nullptr;
-    shape = 0;
+    shape = 2;
   }
   return DAMN_OK;
 }
@@ -446,8 +448,8 @@ static int plan_xwindows(damn_plan *pl, cudaStream_t s) {
     pl->xseg_cap = pl->ntiles;
   }
   const int asz = pl->dtype == DAMN_F64 ? 8 : 4;
-  const int cap_nz = pl->shape == 1 ? CfgLong::CAP_NZ : CfgShort::CAP_NZ;
-  const int xbytes = pl->shape == 1 ? CfgLong::XBYTES : CfgShort::XBYTES;
+  const int cap_nz = pl->shape == 1 ? CfgLong::CAP_NZ : pl->shape == 2 ? CfgSlices::CAP_NZ : CfgShort::CAP_NZ;
+  const int xbytes = pl->shape == 1 ? CfgLong::XBYTES : pl->shape == 2 ? CfgSlices::XBYTES : CfgShort::XBYTES;
   const int blocks = std::min(pl->ntiles, 16 * sm_count());
   k_plan_xseg<<<blocks, 256, 0, s>>>(pl->nrows, pl->ncols, pl->rowptr, pl->idx, pl->fmt, pl->ntiles,
                                      pl->rows_per_tile, pl->d_bounds, cap_nz, xbytes / asz,
@@ -469,7 +471,7 @@ static int plan_xwindows(damn_plan *pl, cudaStream_t s) {
 static int plan_use(damn_plan *pl, int tiling, cudaStream_t s) {
   if (tiling == DAMN_TILING_SLICES) {
     pl->mode = 1;
-    pl->shape = 0;
+    pl->shape = 2;
     pl->rows_per_tile = 0;
     pl->ntiles = pl->ntiles_balanced;
     pl->d_bounds = pl->d_bounds_balanced;
@@ -599,7 +601,7 @@ extern "C" int damn_plan_describe(const damn_plan *plan, damn_plan_desc *h_desc)
   h_desc->ntiles = plan->ntiles;
   h_desc->grid = plan->grid;
   h_desc->stages = plan->stages;
-  h_desc->threads = plan->shape == 1 ? CfgLong::NT : CfgShort::NT;
+  h_desc->threads = plan->shape == 1 ? CfgLong::NT : plan->shape == 2 ? CfgSlices::NT : CfgShort::NT;
   h_desc->row_efficiency = plan->row_eff;
   h_desc->max_row = plan->max_row;
   h_desc->dtype = plan->dtype;

@@ -107,20 +107,28 @@ struct SpmvParams {
   unsigned long long timeout_ns;
 };
 
-template <int NT_, int CAP_NZ_, int CAP_ROWS_, int XBYTES_>
+// NT consumer threads (rows mode: tiles of NT rows); CAP_NZ / CAP_ROWS /
+// XBYTES: capacity of one stage (entries, rows, bytes of staged x); MINB
+// CTAs of NT + 32 threads are meant to share an SM.
+template <int NT_, int CAP_NZ_, int CAP_ROWS_, int XBYTES_, int MINB_>
 struct KCfg {
   static constexpr int NT = NT_, CAP_NZ = CAP_NZ_, CAP_ROWS = CAP_ROWS_, XBYTES = XBYTES_;
+  static constexpr int MINB = MINB_;
 };
 
-// Short rows: 256 consumers (8 warps, two on each SM sub-partition, so the
-// FP64 units of all four carry the same load) + the producer warp, two CTAs
-// per SM (at most 112 registers per thread); row tiles of 256 rows, balanced
-// tiles of up to 512 rows, stages of up to 2048 entries: rows of up to 8
-// entries stay in registers.
-// Long rows: 128 consumers (one warp per sub-partition), stages of 3584
+// Rows mode, short rows: 256 consumers (8 warps: two on each SM
+// sub-partition, so the FP64 units of all four carry the same load) + the
+// producer warp, three CTAs per SM (at most 72 registers per thread) so that
+// six consumer warps per sub-partition keep its FP64 unit fed while the
+// others wait on shared-memory loads.  Tiles of 256 rows, two stages of up
+// to 1792 entries: rows of up to 7 entries stay in registers.
+// Rows mode, long rows: 128 consumers, two CTAs per SM, stages of 3584
 // entries: rows of up to 28 entries.
-using CfgShort = KCfg<256, 2048, 512, 10240>;
-using CfgLong = KCfg<128, 3584, 128, 12288>;
+// Slices mode: 256 consumers, two CTAs per SM, balanced tiles of up to 2048
+// entries and 512 rows.
+using CfgShort = KCfg<256, 1792, 256, 10240, 3>;
+using CfgLong = KCfg<128, 3584, 128, 12288, 2>;
+using CfgSlices = KCfg<256, 2048, 512, 10240, 2>;
 
 constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -608,7 +616,7 @@ __device__ __forceinline__ void tile_slices(const SpmvParams &p, const TileHdr &
 // Kernel
 // ----------------------------------------------------------------------------
 template <bool PLAIN, typename V, typename I, class C>
-__global__ void __launch_bounds__(C::NT + 32, 2) k_spmv(const SpmvParams p) {
+__global__ void __launch_bounds__(C::NT + 32, C::MINB) k_spmv(const SpmvParams p) {
   using A = typename AccOf<V>::type;
   using L = Layout<V, I, C>;
   extern __shared__ __align__(128) unsigned char smem[];
