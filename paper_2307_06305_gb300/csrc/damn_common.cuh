@@ -84,19 +84,33 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
   return ok != 0;
 }
 
+// Same, but the thread may be suspended for up to hint_ns nanoseconds
+// waiting for the phase to complete instead of returning at once, so a
+// waiting warp takes no issue slots from the working ones.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint32_t addr, uint32_t parity,
+                                                      uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Waits for the phase with the given parity to complete, for at most
 // timeout_ns.  On timeout records DAMN_ERR_TIMEOUT in *status and returns
 // false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status,
                                                   uint64_t timeout_ns) {
   const uint32_t a = smem_addr(bar);
-#pragma unroll 1
-  for (int i = 0; i < 16; ++i)
-    if (mbar_try_wait(a, parity)) return true;
+  if (mbar_try_wait(a, parity)) return true;
   const uint64_t t0 = global_timer_ns();
 #pragma unroll 1
   while (true) {
-    if (mbar_try_wait(a, parity)) return true;
+    if (mbar_try_wait_suspend(a, parity, 100000u)) return true;
     if (global_timer_ns() - t0 > timeout_ns) {
       if (status) atomicExch(status, DAMN_ERR_TIMEOUT);
       return false;

@@ -29,8 +29,9 @@ constexpr int kBalancedItems = 2048;
 constexpr int kXGap = 32;           // columns: smaller gaps are staged, not split
 // every tile's row pointers must fit a stage
 static_assert(kBalancedItems / kRowWeight <= CfgSlices::CAP_ROWS, "balanced tiles too tall");
-static_assert(CfgShort::NT <= CfgShort::CAP_ROWS && CfgLong::NT <= CfgLong::CAP_ROWS &&
-                  256 <= CfgSlices::CAP_ROWS,
+static_assert(CfgShort::TILE_ROWS <= CfgShort::CAP_ROWS &&
+                  CfgShortNarrow::TILE_ROWS <= CfgShortNarrow::CAP_ROWS &&
+                  CfgLong::TILE_ROWS <= CfgLong::CAP_ROWS && 256 <= CfgSlices::CAP_ROWS,
               "row tiles too tall");
 
 // ----------------------------------------------------------------------------
@@ -87,7 +88,10 @@ template <typename V, typename I>
 int launch_types(const SpmvParams &p, int shape, cudaStream_t s, int *gs) {
   if (shape == 1) return launch_cfg<V, I, CfgLong>(p, s, gs);
   if (shape == 2) return launch_cfg<V, I, CfgSlices>(p, s, gs);
-  return launch_cfg<V, I, CfgShort>(p, s, gs);
+  if constexpr (sizeof(V) < 8)
+    return launch_cfg<V, I, CfgShortNarrow>(p, s, gs);
+  else
+    return launch_cfg<V, I, CfgShort>(p, s, gs);
 }
 
 int launch_any(const SpmvParams &p, int dtype, int fmt, int shape, cudaStream_t s, int *gs) {
@@ -128,12 +132,13 @@ __global__ void k_plan_bounds(int nrows, const int *__restrict__ rowptr, long lo
 struct PlanStats {
   unsigned long long sum_group_max;  // sum over 32-row groups of the longest row
   int max_row;
-  int max_tile_short;                // most entries in a CfgShort::NT-row tile
-  int max_tile_long;                 // most entries in a CfgLong::NT-row tile
+  int max_tile_short;                // most entries in a short-rows tile
+  int max_tile_long;                 // most entries in a long-rows tile
   int pad;
 };
 
-__global__ void k_plan_stats(int nrows, const int *__restrict__ rowptr, PlanStats *st) {
+__global__ void k_plan_stats(int nrows, const int *__restrict__ rowptr, int tile_short,
+                             int tile_long, PlanStats *st) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int len = 0;
   if (i < nrows) len = rowptr[i + 1] - rowptr[i];
@@ -143,12 +148,12 @@ __global__ void k_plan_stats(int nrows, const int *__restrict__ rowptr, PlanStat
     atomicAdd(&st->sum_group_max, (unsigned long long)gmax);
     atomicMax(&st->max_row, gmax);
   }
-  if (i < nrows && i % CfgShort::NT == 0) {
-    const int r1 = (int)min((long long)nrows, i + CfgShort::NT);
+  if (i < nrows && i % tile_short == 0) {
+    const int r1 = (int)min((long long)nrows, i + tile_short);
     atomicMax(&st->max_tile_short, rowptr[r1] - rowptr[i]);
   }
-  if (i < nrows && i % CfgLong::NT == 0) {
-    const int r1 = (int)min((long long)nrows, i + CfgLong::NT);
+  if (i < nrows && i % tile_long == 0) {
+    const int r1 = (int)min((long long)nrows, i + tile_long);
     atomicMax(&st->max_tile_long, rowptr[r1] - rowptr[i]);
   }
 }
@@ -321,6 +326,19 @@ namespace damn {
 
 int spmv_max_grid() { return 8 * sm_count(); }
 
+// Tile height, stage entry capacity and staged-x capacity of the kernel
+// configuration a plan shape uses for a value type (must match launch_types).
+struct CfgGeom {
+  int tile_rows, cap_nz, xcap;
+};
+static CfgGeom cfg_geom(int shape, int dtype) {
+  if (shape == 1) return {CfgLong::TILE_ROWS, CfgLong::CAP_NZ, CfgLong::XCAP};
+  if (shape == 2) return {0, CfgSlices::CAP_NZ, CfgSlices::XCAP};
+  if (dtype != DAMN_F64)
+    return {CfgShortNarrow::TILE_ROWS, CfgShortNarrow::CAP_NZ, CfgShortNarrow::XCAP};
+  return {CfgShort::TILE_ROWS, CfgShort::CAP_NZ, CfgShort::XCAP};
+}
+
 static int make_params(const SpmvCall &c, const damn_plan *plan, SpmvParams &p, int &shape) {
   std::memset(&p, 0, sizeof(p));
   p.nrows = c.nrows;
@@ -448,11 +466,12 @@ static int plan_xwindows(damn_plan *pl, cudaStream_t s) {
     pl->xseg_cap = pl->ntiles;
   }
   const int asz = pl->dtype == DAMN_F64 ? 8 : 4;
-  const int cap_nz = pl->shape == 1 ? CfgLong::CAP_NZ : pl->shape == 2 ? CfgSlices::CAP_NZ : CfgShort::CAP_NZ;
-  const int xbytes = pl->shape == 1 ? CfgLong::XBYTES : pl->shape == 2 ? CfgSlices::XBYTES : CfgShort::XBYTES;
+  const CfgGeom geo = cfg_geom(pl->shape, pl->dtype);
+  const int cap_nz = geo.cap_nz;
+  const int xcap = geo.xcap;
   const int blocks = std::min(pl->ntiles, 16 * sm_count());
   k_plan_xseg<<<blocks, 256, 0, s>>>(pl->nrows, pl->ncols, pl->rowptr, pl->idx, pl->fmt, pl->ntiles,
-                                     pl->rows_per_tile, pl->d_bounds, cap_nz, xbytes / asz,
+                                     pl->rows_per_tile, pl->d_bounds, cap_nz, xcap,
                                      16 / asz, pl->d_xseg);
   DAMN_CHECK_LAUNCH("k_plan_xseg");
   int *d_cnt = nullptr;
@@ -479,7 +498,7 @@ static int plan_use(damn_plan *pl, int tiling, cudaStream_t s) {
     const int shape = tiling == DAMN_TILING_ROWS_LONG ? 1 : 0;
     pl->mode = 0;
     pl->shape = shape;
-    pl->rows_per_tile = shape == 1 ? CfgLong::NT : CfgShort::NT;
+    pl->rows_per_tile = cfg_geom(shape, pl->dtype).tile_rows;
     pl->ntiles = (pl->nrows + pl->rows_per_tile - 1) / pl->rows_per_tile;
     pl->d_bounds = nullptr;
   }
@@ -521,7 +540,9 @@ extern "C" int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const
   if (nrows > 0) {
     k_plan_bounds<<<(pl->ntiles_balanced + 1 + 255) / 256, 256, 0, s>>>(
         nrows, rowptr, D, pl->ntiles_balanced, pl->d_bounds_balanced);
-    k_plan_stats<<<(nrows + 255) / 256, 256, 0, s>>>(nrows, rowptr, d_st);
+    k_plan_stats<<<(nrows + 255) / 256, 256, 0, s>>>(nrows, rowptr,
+                                                     cfg_geom(0, dtype).tile_rows,
+                                                     cfg_geom(1, dtype).tile_rows, d_st);
   }
   PlanStats h{};
   cudaMemcpyAsync(&h, d_st, sizeof(h), cudaMemcpyDeviceToHost, s);
@@ -536,9 +557,9 @@ extern "C" int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const
   // Heuristic choice: one row per thread when rows are uniform inside 32-row
   // groups and a row block fits a stage; balanced slices otherwise.
   int tiling = DAMN_TILING_SLICES;
-  if (pl->row_eff >= 0.85 && pl->max_tile_short <= CfgShort::CAP_NZ)
+  if (pl->row_eff >= 0.85 && pl->max_tile_short <= cfg_geom(0, dtype).cap_nz)
     tiling = DAMN_TILING_ROWS;
-  else if (pl->row_eff >= 0.85 && pl->max_tile_long <= CfgLong::CAP_NZ)
+  else if (pl->row_eff >= 0.85 && pl->max_tile_long <= cfg_geom(1, dtype).cap_nz)
     tiling = DAMN_TILING_ROWS_LONG;
   int rc = plan_use(pl, tiling, s);
   if (rc) { plan_free_device(pl); delete pl; return rc; }

@@ -107,28 +107,36 @@ struct SpmvParams {
   unsigned long long timeout_ns;
 };
 
-// NT consumer threads (rows mode: tiles of NT rows); CAP_NZ / CAP_ROWS /
-// XBYTES: capacity of one stage (entries, rows, bytes of staged x); MINB
-// CTAs of NT + 32 threads are meant to share an SM.
-template <int NT_, int CAP_NZ_, int CAP_ROWS_, int XBYTES_, int MINB_>
+// NT consumer threads; rows mode: tiles of TILE_ROWS = RPT * NT rows, each
+// thread computing RPT of them.  CAP_NZ / CAP_ROWS / XCAP: capacity of one
+// stage (entries, rows, staged x elements).  MINB CTAs of NT + 32 threads are
+// meant to share an SM.
+template <int NT_, int CAP_NZ_, int CAP_ROWS_, int XCAP_, int MINB_, int RPT_ = 1>
 struct KCfg {
-  static constexpr int NT = NT_, CAP_NZ = CAP_NZ_, CAP_ROWS = CAP_ROWS_, XBYTES = XBYTES_;
-  static constexpr int MINB = MINB_;
+  static constexpr int NT = NT_, CAP_NZ = CAP_NZ_, CAP_ROWS = CAP_ROWS_, XCAP = XCAP_;
+  static constexpr int MINB = MINB_, RPT = RPT_;
+  static constexpr int TILE_ROWS = NT * RPT;
 };
 
-// Rows mode, short rows: 256 consumers (8 warps: two on each SM
+// Rows mode, short rows, FP64 values: 256 consumers (8 warps: two on each SM
 // sub-partition, so the FP64 units of all four carry the same load) + the
 // producer warp, three CTAs per SM (at most 72 registers per thread) so that
 // six consumer warps per sub-partition keep its FP64 unit fed while the
 // others wait on shared-memory loads.  Tiles of 256 rows, two stages of up
 // to 1792 entries: rows of up to 7 entries stay in registers.
+// Rows mode, short rows, FP32 / BF16 values: the same CTAs with tiles of 512
+// rows, two rows per thread loaded together (their FP32 operands fit the
+// registers), so each warp pays the shared-memory latency chain once per two
+// rows and the producer -- whose bulk copies cost a fixed ~170 cycles each to
+// issue -- starts half as many tiles per row.
 // Rows mode, long rows: 128 consumers, two CTAs per SM, stages of 3584
 // entries: rows of up to 28 entries.
 // Slices mode: 256 consumers, two CTAs per SM, balanced tiles of up to 2048
 // entries and 512 rows.
-using CfgShort = KCfg<256, 1792, 256, 10240, 3>;
-using CfgLong = KCfg<128, 3584, 128, 12288, 2>;
-using CfgSlices = KCfg<256, 2048, 512, 10240, 2>;
+using CfgShort = KCfg<256, 1792, 256, 1280, 3, 1>;
+using CfgShortNarrow = KCfg<256, 3584, 512, 2560, 3, 2>;
+using CfgLong = KCfg<128, 3584, 128, 1536, 2, 1>;
+using CfgSlices = KCfg<256, 2048, 512, 1280, 2, 1>;
 
 constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -137,7 +145,7 @@ template <typename V, typename I, class C>
 struct Layout {
   using A = typename AccOf<V>::type;
   static constexpr int EV = 16 / (int)sizeof(V), EI = 16 / (int)sizeof(I), EX = 16 / (int)sizeof(A);
-  static constexpr int XCAP = C::XBYTES / (int)sizeof(A);  // staged x elements per tile
+  static constexpr int XCAP = C::XCAP;  // staged x elements per tile
   static constexpr size_t RP_BYTES = align_up((C::CAP_ROWS + 1 + 8) * 4, 128);
   static constexpr size_t V_BYTES = align_up((C::CAP_NZ + 2 * EV) * sizeof(V), 128);
   static constexpr size_t I_BYTES = align_up((C::CAP_NZ + 2 * EI) * sizeof(I), 128);
@@ -473,7 +481,7 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
   using L = Layout<V, I, C>;
   using A = typename AccOf<V>::type;
   constexpr bool DA = sizeof(I) == 2;
-  constexpr int U = C::CAP_NZ / C::NT;
+  constexpr int U = C::CAP_NZ / C::TILE_ROWS;
   const int lane = threadIdx.x & 31;
   int j = 0;
   for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++j) {
@@ -496,35 +504,50 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
     const I *is = reinterpret_cast<const I *>(st + L::OFF_I) + h1.z;
     const A *xs = reinterpret_cast<const A *>(st + L::OFF_X);
     const int r0 = h0.x, nr = h0.y, k0 = h0.z;
-    A av[U], xv[U];
-    int b = 0, cnt = 0;
-    if (ctid < nr) {
-      b = rp[ctid] - k0;
-      cnt = rp[ctid + 1] - k0 - b;
+    // the thread's RPT rows: operands of all of them into registers first
+    A av[C::RPT][U], xv[C::RPT][U];
+    int b[C::RPT], cnt[C::RPT];
+    bool fits = true;
+#pragma unroll
+    for (int rr = 0; rr < C::RPT; ++rr) {
+      const int lr = ctid + rr * C::NT;
+      b[rr] = 0;
+      cnt[rr] = 0;
+      if (lr < nr) {
+        b[rr] = rp[lr] - k0;
+        cnt[rr] = rp[lr + 1] - k0 - b[rr];
+      }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (u < cnt) {
-          const int cl = DA ? ctid + static_cast<int>(is[b + u]) : static_cast<int>(is[b + u]) - r0;
-          av[u] = to_acc(vs[b + u]);
-          xv[u] = xs[xm.slot(cl)];
+        if (u < cnt[rr]) {
+          const int cl = DA ? lr + static_cast<int>(is[b[rr] + u])
+                            : static_cast<int>(is[b[rr] + u]) - r0;
+          av[rr][u] = to_acc(vs[b[rr] + u]);
+          xv[rr][u] = xs[xm.slot(cl)];
         }
       }
+      fits = fits && cnt[rr] <= U;
     }
-    const bool fits = __all_sync(0xffffffffu, cnt <= U);
+    // every row of this warp in registers: hand the stage back at once
+    fits = __all_sync(0xffffffffu, fits);
     if (fits) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
     }
-    if (ctid < nr) {
-      A acc = 0;
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (u < cnt) acc = fma_acc(av[u], xv[u], acc);
-      for (int q = b + U; q < b + cnt; ++q) {  // only when !fits
-        const int cl = DA ? ctid + static_cast<int>(is[q]) : static_cast<int>(is[q]) - r0;
-        acc = fma_acc(to_acc(vs[q]), xs[xm.slot(cl)], acc);
+    for (int rr = 0; rr < C::RPT; ++rr) {
+      const int lr = ctid + rr * C::NT;
+      if (lr < nr) {
+        A acc = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (u < cnt[rr]) acc = fma_acc(av[rr][u], xv[rr][u], acc);
+        for (int q = b[rr] + U; q < b[rr] + cnt[rr]; ++q) {  // rows longer than U
+          const int cl = DA ? lr + static_cast<int>(is[q]) : static_cast<int>(is[q]) - r0;
+          acc = fma_acc(to_acc(vs[q]), xs[xm.slot(cl)], acc);
+        }
+        store_row<PLAIN>(p, r0 + lr, acc, dsum);
       }
-      store_row<PLAIN>(p, r0 + ctid, acc, dsum);
     }
     if (!fits) {
       __syncwarp();
