@@ -401,6 +401,7 @@ def section_batched(D, torch, dev, reps):
                         "speedup_vs_per_matrix_graph": round(t_pg / t_g, 3),
                         "gflops": round(flops / t_g / 1e9, 1), "bytes": nbytes,
                         "tuned": {"rows_per_item": desc["tile_items"], "threads": desc["threads"],
+                                  "entry_lanes": desc["entry_lanes"],
                                   "grid": desc["grid"]}}
             plan.close()
             del g, mats, plan

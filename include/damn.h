@@ -301,7 +301,10 @@ int damn_cg_ir(int32_t n, int64_t nnz, const int32_t *rowptr, const int16_t *off
 /* ------------------------------------------------------------------------ */
 
 /* Y = A X for one DA-CSR-16 matrix, X row-major ncols x k, Y row-major
- * nrows x k (1 <= k <= 64).  dtype F64 (X, Y FP64) or F32 (X, Y FP32). */
+ * nrows x k (1 <= k <= 64).  dtype F64 (X, Y FP64) or F32 (X, Y FP32).
+ * Each row's entries are split over E lanes (E chosen from nnz / nrows, about
+ * four entries per lane and pass) whose partial sums are added in a fixed
+ * butterfly order; results depend only on (k, E). */
 int damn_spmm_dacsr16(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
                       const int16_t *off, const void *val, int dtype, int32_t k, const void *X,
                       void *Y, void *stream);
@@ -320,6 +323,8 @@ typedef struct damn_batch_plan damn_batch_plan;
 
 typedef struct {
   int32_t count, k, dtype, ntiles, grid, threads, tile_items, graph_ready;
+  int32_t entry_lanes;     /* lanes splitting each row's entries (summation shape) */
+  int32_t reserved;
   double tune_ms;          /* best time measured by the autotuner (0 if none) */
 } damn_batch_desc;
 

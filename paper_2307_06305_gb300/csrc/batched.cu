@@ -5,16 +5,17 @@
 // i of row r multiplies row r + off[i] of X (the shifted view of Listing 2,
 // Section 4, applied to each column of X).
 //
-// Work decomposition: a warp takes R = 32 / L rows at a time, L = the largest
-// power of two <= min(k, 32) lanes per row; lane l of a row group owns the
-// right-hand-side columns l, l + L, ... (at most two), so every FMA lane does
-// useful work and the X loads of a row group are contiguous.  Each lane walks
-// its row's entries in stored order (Listing 2 order per column), four at a
-// time so that four entries' loads are in flight.
+// Work decomposition: a row group of L * E lanes computes one row, L = the
+// largest power of two <= min(k, 32): column lane l owns the right-hand-side
+// columns l, l + L (at most two), so the X loads of a row group are
+// contiguous; entry lane e walks the row's entries e, e + E, ... (E = 1:
+// Listing 2 order per column), four steps at a time so that several loads
+// are in flight, and the E partial sums are added by a butterfly.  A warp
+// takes 32 / (L * E) rows per pass.
 //
 // Batched launch: the host builds a list of (matrix, first row) work items
 // of rows_per_item rows each; persistent warps take items round-robin.  The
-// plan's autotuner times a few (rows_per_item, threads) shapes on the real
+// plan's autotuner times the (rows_per_item, E, threads) shapes on the real
 // operands and keeps the fastest; the launch is captured in a CUDA graph.
 #include <algorithm>
 #include <climits>
@@ -36,27 +37,38 @@ struct DevDesc {  // device copy of damn_mat_desc
   void *Y;
 };
 
-// y[row, jcols] for one row group; T: FP64 or FP32 (values and vectors)
-template <typename T, int L, int J>
-__device__ __forceinline__ void spmm_row(const DevDesc &d, int row, int k, int li) {
+// One row group of G = L * E lanes computes y[row, :]: column lane li owns
+// the right-hand-side columns li, li + L (at most J of them), entry lane ei
+// takes the row's entries ei, ei + E, ... in stored order; the E partial sums
+// of a column are then added by a butterfly over the entry lanes (a fixed
+// order, so results depend only on (L, J, E)).  All lanes of the warp call
+// this together (valid == false for a lane whose row does not exist).
+template <typename T, int L, int J, int E>
+__device__ __forceinline__ void spmm_row(const DevDesc &d, int row, bool valid, int k, int li,
+                                         int ei) {
   const T *val = static_cast<const T *>(d.val);
   const T *X = static_cast<const T *>(d.X);
   T *Y = static_cast<T *>(d.Y);
-  const int b = __ldg(d.rowptr + row), e = __ldg(d.rowptr + row + 1);
+  int b = 0, e = 0;
+  if (valid) {
+    b = __ldg(d.rowptr + row);
+    e = __ldg(d.rowptr + row + 1);
+  }
   T acc[J];
 #pragma unroll
   for (int jj = 0; jj < J; ++jj) acc[jj] = T(0);
   constexpr int U = 4;
-  for (int q = b; q < e; q += U) {
+  for (int q0 = b + ei; q0 < e; q0 += U * E) {
     T v[U];
     int c[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
+      const int q = q0 + u * E;
       v[u] = T(0);
       c[u] = row;
-      if (q + u < e) {
-        v[u] = __ldg(val + q + u);
-        c[u] = row + static_cast<int>(__ldg(d.off + q + u));
+      if (q < e) {
+        v[u] = __ldg(val + q);
+        c[u] = row + static_cast<int>(__ldg(d.off + q));
       }
     }
     T xv[U][J];
@@ -65,46 +77,53 @@ __device__ __forceinline__ void spmm_row(const DevDesc &d, int row, int k, int l
 #pragma unroll
       for (int jj = 0; jj < J; ++jj) {
         const int j = li + jj * L;
-        xv[u][jj] = (q + u < e && j < k) ? __ldg(X + (size_t)c[u] * k + j) : T(0);
+        xv[u][jj] = (q0 + u * E < e && j < k) ? __ldg(X + (size_t)c[u] * k + j) : T(0);
       }
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (q + u < e)
+      if (q0 + u * E < e)
 #pragma unroll
         for (int jj = 0; jj < J; ++jj) acc[jj] = fma_acc(v[u], xv[u][jj], acc[jj]);
   }
 #pragma unroll
-  for (int jj = 0; jj < J; ++jj) {
-    const int j = li + jj * L;
-    if (j < k) Y[(size_t)row * k + j] = acc[jj];
+  for (int o = L; o < L * E; o <<= 1)
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) acc[jj] += __shfl_xor_sync(0xffffffffu, acc[jj], o);
+  if (valid && ei == 0) {
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) {
+      const int j = li + jj * L;
+      if (j < k) Y[(size_t)row * k + j] = acc[jj];
+    }
   }
 }
 
 // Batched: items[i] = {matrix, first row}; rows_per_item rows per item.
-template <typename T, int L, int J>
+template <typename T, int L, int J, int E>
 __global__ void k_spmm_batched(const DevDesc *descs, const int2 *items, int nitems, int k,
                                int rows_per_item) {
-  constexpr int R = 32 / L;
-  const int lane = threadIdx.x & 31, grp = lane / L, li = lane % L;
+  constexpr int G = L * E, R = 32 / G;
+  const int lane = threadIdx.x & 31, grp = lane / G, li = lane % L, ei = (lane % G) / L;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long it = warp; it < nitems; it += nwarps) {
     const int2 item = items[it];
     const DevDesc d = descs[item.x];
     const int rend = min(item.y + rows_per_item, d.nrows);
-    for (int row = item.y + grp; row < rend; row += R) spmm_row<T, L, J>(d, row, k, li);
+    for (int base = item.y; base < rend; base += R)  // warp-uniform bound: shuffles
+      spmm_row<T, L, J, E>(d, base + grp, base + grp < rend, k, li, ei);
   }
 }
 
 // One matrix: the rows are the work, no descriptor array.
-template <typename T, int L, int J>
+template <typename T, int L, int J, int E>
 __global__ void k_spmm_single(DevDesc d, int k) {
-  constexpr int R = 32 / L;
-  const int lane = threadIdx.x & 31, grp = lane / L, li = lane % L;
+  constexpr int G = L * E, R = 32 / G;
+  const int lane = threadIdx.x & 31, grp = lane / G, li = lane % L, ei = (lane % G) / L;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long row = warp * R + grp; row < d.nrows; row += nwarps * R)
-    spmm_row<T, L, J>(d, static_cast<int>(row), k, li);
+  for (long long base = warp * R; base < d.nrows; base += nwarps * R)
+    spmm_row<T, L, J, E>(d, static_cast<int>(base + grp), base + grp < d.nrows, k, li, ei);
 }
 
 int lanes_for(int k) {
@@ -113,54 +132,90 @@ int lanes_for(int k) {
   return L;
 }
 
-template <typename T, int L>
-int launch_single_l(const DevDesc &d, int k, cudaStream_t s) {
-  const int R = 32 / L;
+// Entry lanes for one matrix without timing: about four entries per lane
+// and pass, at most 32 / L.
+int entry_lanes_for(const DevDesc &d, int L) {
+  const double avg = d.nrows > 0 ? (double)d.nnz / d.nrows : 0.0;
+  int E = 1;
+  while (E * 2 * L <= 32 && E * 2 * 4 <= avg) E *= 2;
+  return E;
+}
+
+template <typename T, int L, int E>
+int launch_single_le(const DevDesc &d, int k, cudaStream_t s) {
+  constexpr int R = 32 / (L * E);
   const long long warps_needed = (d.nrows + R - 1) / R;
   const int threads = 256;
   const int blocks = (int)std::max(1LL, std::min<long long>(8LL * sm_count(),
                                                             (warps_needed * 32 + threads - 1) / threads));
   if ((k + L - 1) / L <= 1)
-    k_spmm_single<T, L, 1><<<blocks, threads, 0, s>>>(d, k);
+    k_spmm_single<T, L, 1, E><<<blocks, threads, 0, s>>>(d, k);
   else
-    k_spmm_single<T, L, 2><<<blocks, threads, 0, s>>>(d, k);
+    k_spmm_single<T, L, 2, E><<<blocks, threads, 0, s>>>(d, k);
   DAMN_CHECK_LAUNCH("k_spmm_single");
   return DAMN_OK;
 }
 
+template <typename T, int L>
+int launch_single_l(const DevDesc &d, int k, int E, cudaStream_t s) {
+  if constexpr (L <= 16)
+    if (E >= 2) {
+      if constexpr (L <= 4)
+        if (E >= 8) return launch_single_le<T, L, 8>(d, k, s);
+      if constexpr (L <= 8)
+        if (E >= 4) return launch_single_le<T, L, 4>(d, k, s);
+      return launch_single_le<T, L, 2>(d, k, s);
+    }
+  return launch_single_le<T, L, 1>(d, k, s);
+}
+
 template <typename T>
-int launch_single(const DevDesc &d, int k, cudaStream_t s) {
+int launch_single(const DevDesc &d, int k, int E, cudaStream_t s) {
   switch (lanes_for(k)) {
-    case 1: return launch_single_l<T, 1>(d, k, s);
-    case 2: return launch_single_l<T, 2>(d, k, s);
-    case 4: return launch_single_l<T, 4>(d, k, s);
-    case 8: return launch_single_l<T, 8>(d, k, s);
-    case 16: return launch_single_l<T, 16>(d, k, s);
-    default: return launch_single_l<T, 32>(d, k, s);
+    case 1: return launch_single_l<T, 1>(d, k, E, s);
+    case 2: return launch_single_l<T, 2>(d, k, E, s);
+    case 4: return launch_single_l<T, 4>(d, k, E, s);
+    case 8: return launch_single_l<T, 8>(d, k, E, s);
+    case 16: return launch_single_l<T, 16>(d, k, E, s);
+    default: return launch_single_l<T, 32>(d, k, E, s);
   }
 }
 
-template <typename T, int L>
-int launch_batched_l(const DevDesc *descs, const int2 *items, int nitems, int k, int rpi,
-                     int blocks, int threads, cudaStream_t s) {
+template <typename T, int L, int E>
+int launch_batched_le(const DevDesc *descs, const int2 *items, int nitems, int k, int rpi,
+                      int blocks, int threads, cudaStream_t s) {
   if ((k + L - 1) / L <= 1)
-    k_spmm_batched<T, L, 1><<<blocks, threads, 0, s>>>(descs, items, nitems, k, rpi);
+    k_spmm_batched<T, L, 1, E><<<blocks, threads, 0, s>>>(descs, items, nitems, k, rpi);
   else
-    k_spmm_batched<T, L, 2><<<blocks, threads, 0, s>>>(descs, items, nitems, k, rpi);
+    k_spmm_batched<T, L, 2, E><<<blocks, threads, 0, s>>>(descs, items, nitems, k, rpi);
   DAMN_CHECK_LAUNCH("k_spmm_batched");
   return DAMN_OK;
 }
 
+template <typename T, int L>
+int launch_batched_l(const DevDesc *descs, const int2 *items, int nitems, int k, int rpi, int E,
+                     int blocks, int threads, cudaStream_t s) {
+  if constexpr (L <= 16)
+    if (E >= 2) {
+      if constexpr (L <= 4)
+        if (E >= 8) return launch_batched_le<T, L, 8>(descs, items, nitems, k, rpi, blocks, threads, s);
+      if constexpr (L <= 8)
+        if (E >= 4) return launch_batched_le<T, L, 4>(descs, items, nitems, k, rpi, blocks, threads, s);
+      return launch_batched_le<T, L, 2>(descs, items, nitems, k, rpi, blocks, threads, s);
+    }
+  return launch_batched_le<T, L, 1>(descs, items, nitems, k, rpi, blocks, threads, s);
+}
+
 template <typename T>
-int launch_batched(const DevDesc *descs, const int2 *items, int nitems, int k, int rpi, int blocks,
-                   int threads, cudaStream_t s) {
+int launch_batched(const DevDesc *descs, const int2 *items, int nitems, int k, int rpi, int E,
+                   int blocks, int threads, cudaStream_t s) {
   switch (lanes_for(k)) {
-    case 1: return launch_batched_l<T, 1>(descs, items, nitems, k, rpi, blocks, threads, s);
-    case 2: return launch_batched_l<T, 2>(descs, items, nitems, k, rpi, blocks, threads, s);
-    case 4: return launch_batched_l<T, 4>(descs, items, nitems, k, rpi, blocks, threads, s);
-    case 8: return launch_batched_l<T, 8>(descs, items, nitems, k, rpi, blocks, threads, s);
-    case 16: return launch_batched_l<T, 16>(descs, items, nitems, k, rpi, blocks, threads, s);
-    default: return launch_batched_l<T, 32>(descs, items, nitems, k, rpi, blocks, threads, s);
+    case 1: return launch_batched_l<T, 1>(descs, items, nitems, k, rpi, E, blocks, threads, s);
+    case 2: return launch_batched_l<T, 2>(descs, items, nitems, k, rpi, E, blocks, threads, s);
+    case 4: return launch_batched_l<T, 4>(descs, items, nitems, k, rpi, E, blocks, threads, s);
+    case 8: return launch_batched_l<T, 8>(descs, items, nitems, k, rpi, E, blocks, threads, s);
+    case 16: return launch_batched_l<T, 16>(descs, items, nitems, k, rpi, E, blocks, threads, s);
+    default: return launch_batched_l<T, 32>(descs, items, nitems, k, rpi, E, blocks, threads, s);
   }
 }
 
@@ -182,6 +237,7 @@ struct damn_batch_plan {
   int2 *d_items;
   int nitems;
   int rows_per_item;
+  int entry_lanes;         // E: lanes splitting each row's entries
   int threads, blocks;
   std::vector<int> nrows;  // per matrix, to rebuild items
   cudaGraphExec_t graph;
@@ -207,9 +263,9 @@ static int batch_launch(const damn_batch_plan *pl, cudaStream_t s) {
   if (pl->nitems == 0) return DAMN_OK;
   if (pl->dtype == DAMN_F64)
     return launch_batched<double>(pl->d_descs, pl->d_items, pl->nitems, pl->k, pl->rows_per_item,
-                                  pl->blocks, pl->threads, s);
+                                  pl->entry_lanes, pl->blocks, pl->threads, s);
   return launch_batched<float>(pl->d_descs, pl->d_items, pl->nitems, pl->k, pl->rows_per_item,
-                               pl->blocks, pl->threads, s);
+                               pl->entry_lanes, pl->blocks, pl->threads, s);
 }
 
 static void batch_free(damn_batch_plan *pl) {
@@ -232,7 +288,8 @@ extern "C" int damn_spmm_dacsr16(int32_t nrows, int32_t ncols, int64_t nnz, cons
   if (nrows == 0) return DAMN_OK;
   DevDesc d{nrows, ncols, nnz, rowptr, off, val, X, Y};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return dtype == DAMN_F64 ? launch_single<double>(d, k, s) : launch_single<float>(d, k, s);
+  const int E = entry_lanes_for(d, lanes_for(k));
+  return dtype == DAMN_F64 ? launch_single<double>(d, k, E, s) : launch_single<float>(d, k, E, s);
 }
 
 extern "C" int damn_batch_plan_create(int32_t count, const damn_mat_desc *h_descs, int32_t k,
@@ -266,38 +323,49 @@ extern "C" int damn_batch_plan_create(int32_t count, const damn_mat_desc *h_desc
     e = cudaMemcpy(pl->d_descs, dd.data(), sizeof(DevDesc) * count, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(cuda_error(e, "damn_batch_plan_create: cudaMemcpy"));
   }
-  // default shape: one row group of 32/L rows per warp pass, items of 256 rows
+  // default shape: about four entries per lane and pass, items of 256 rows
+  long long tot_rows = 0, tot_nnz = 0;
+  for (int m = 0; m < count; ++m) { tot_rows += h_descs[m].nrows; tot_nnz += h_descs[m].nnz; }
+  const int L = lanes_for(k);
+  {
+    DevDesc avg{(int)std::min<long long>(tot_rows, INT_MAX), 0, tot_nnz, nullptr, nullptr, nullptr,
+                nullptr, nullptr};
+    pl->entry_lanes = entry_lanes_for(avg, L);
+  }
   int rc = batch_build_items(pl, 256);
   if (rc) return fail(rc);
   pl->threads = 256;
   pl->blocks = std::max(1, std::min(8 * sm_count(), (pl->nitems * 32 + 255) / 256));
   if (autotune && pl->nitems > 0) {
-    const int rpis[3] = {64, 256, 1024};
+    const int rpis[2] = {64, 256};
     const int tps[2] = {128, 256};
     float best = 1e30f;
-    int best_rpi = 256, best_tp = 256;
+    int best_rpi = 256, best_tp = 256, best_e = pl->entry_lanes;
     cudaEvent_t e0, e1;
     DAMN_CUDA(cudaEventCreate(&e0));
     DAMN_CUDA(cudaEventCreate(&e1));
-    for (int a = 0; a < 3 && rc == DAMN_OK; ++a) {
+    for (int a = 0; a < 2 && rc == DAMN_OK; ++a) {
       rc = batch_build_items(pl, rpis[a]);
-      for (int b = 0; b < 2 && rc == DAMN_OK; ++b) {
-        pl->threads = tps[b];
-        const int warps_per_block = pl->threads / 32;
-        pl->blocks = std::max(1, std::min(16 * sm_count(),
-                                          (pl->nitems + warps_per_block - 1) / warps_per_block));
-        rc = batch_launch(pl, s);  // warm
-        float tmin = 1e30f;
-        for (int r = 0; r < 3 && rc == DAMN_OK; ++r) {
-          cudaEventRecord(e0, s);
-          rc = batch_launch(pl, s);
-          cudaEventRecord(e1, s);
-          cudaEventSynchronize(e1);
-          float ms = 0;
-          cudaEventElapsedTime(&ms, e0, e1);
-          tmin = std::min(tmin, ms);
+      for (int E = 1; E * L <= 32 && E <= 8 && rc == DAMN_OK; E *= 2) {
+        pl->entry_lanes = E;
+        for (int b = 0; b < 2 && rc == DAMN_OK; ++b) {
+          pl->threads = tps[b];
+          const int warps_per_block = pl->threads / 32;
+          pl->blocks = std::max(1, std::min(16 * sm_count(),
+                                            (pl->nitems + warps_per_block - 1) / warps_per_block));
+          rc = batch_launch(pl, s);  // warm
+          float tmin = 1e30f;
+          for (int r = 0; r < 3 && rc == DAMN_OK; ++r) {
+            cudaEventRecord(e0, s);
+            rc = batch_launch(pl, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            tmin = std::min(tmin, ms);
+          }
+          if (tmin < best) { best = tmin; best_rpi = rpis[a]; best_tp = tps[b]; best_e = E; }
         }
-        if (tmin < best) { best = tmin; best_rpi = rpis[a]; best_tp = tps[b]; }
       }
     }
     cudaEventDestroy(e0);
@@ -305,6 +373,7 @@ extern "C" int damn_batch_plan_create(int32_t count, const damn_mat_desc *h_desc
     if (rc) return fail(rc);
     rc = batch_build_items(pl, best_rpi);
     if (rc) return fail(rc);
+    pl->entry_lanes = best_e;
     pl->threads = best_tp;
     const int wpb = pl->threads / 32;
     pl->blocks = std::max(1, std::min(16 * sm_count(), (pl->nitems + wpb - 1) / wpb));
@@ -342,6 +411,8 @@ extern "C" int damn_batch_plan_describe(const damn_batch_plan *plan, damn_batch_
   h->threads = plan->threads;
   h->tile_items = plan->rows_per_item;
   h->graph_ready = plan->graph ? 1 : 0;
+  h->entry_lanes = plan->entry_lanes;
+  h->reserved = 0;
   h->tune_ms = plan->tune_ms;
   return DAMN_OK;
 }

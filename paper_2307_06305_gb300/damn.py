@@ -80,7 +80,8 @@ class damn_mat_desc(ctypes.Structure):
 
 class damn_batch_desc(ctypes.Structure):
     _fields_ = [("count", I32), ("k", I32), ("dtype", I32), ("ntiles", I32), ("grid", I32),
-                ("threads", I32), ("tile_items", I32), ("graph_ready", I32), ("tune_ms", F64)]
+                ("threads", I32), ("tile_items", I32), ("graph_ready", I32),
+                ("entry_lanes", I32), ("reserved", I32), ("tune_ms", F64)]
 
 
 def _sig(name, res, args):

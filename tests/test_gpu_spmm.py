@@ -16,6 +16,22 @@ def _t(dev, a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
 
 
+def _lanes(k):
+    L = 1
+    while L * 2 <= min(k, 32):
+        L *= 2
+    return L
+
+
+def _entry_lanes(nrows, nnz, L):
+    """The single-matrix call's choice: about four entries per lane and pass."""
+    avg = nnz / nrows if nrows else 0.0
+    E = 1
+    while E * 2 * L <= 32 and E * 2 * 4 <= avg:
+        E *= 2
+    return E
+
+
 def _check_cols(n, rp, off, val, X, Y, u):
     """Every column against the oracle's FP64 product (both within their own
     bounds of the exact result); the first and last column against the exact
@@ -71,12 +87,20 @@ def test_batched_matches_single_and_oracle(D, cuda_dev, k, dt):
         m[4].fill_(float("nan"))
     plan.graph_launch()
     torch.cuda.synchronize()
+    E = desc["entry_lanes"]
+    L = _lanes(k)
+    assert E >= 1 and L * E <= 32
     for (rp, off, tv, tX, Y), d0 in zip(mats, direct):
         assert torch.equal(Y, d0)
         Ys = torch.empty_like(Y)
         D.damn_spmm_dacsr16(rp, off, tv, tX, Ys)
         torch.cuda.synchronize()
-        assert torch.equal(Ys, Y)   # same per-row summation order
+        if _entry_lanes(rp.numel() - 1, off.numel(), L) == E:
+            assert torch.equal(Ys, Y)   # same summation shape (k, E): same bits
+        else:
+            scale = Y.abs().max().item() + 1.0
+            tol = 1e-12 if dt == torch.float64 else 1e-4
+            assert torch.allclose(Ys, Y, rtol=0, atol=tol * scale)
     u = OS.U64 if dt == torch.float64 else OS.U32
     for (n, rp, off, val, X), (_, _, tv, _, Y) in zip(ref[:4], mats[:4]):
         valq = val.astype(np.float32).astype(np.float64) if dt == torch.float32 else val
