@@ -59,6 +59,7 @@ extern "C" {
 
 #define DAMN_FMT_CSR32   0
 #define DAMN_FMT_DACSR16 1
+#define DAMN_FMT_DACSR8  2
 
 /* Message describing the last error reported to the calling host thread. */
 const char *damn_last_error(void);
@@ -107,6 +108,14 @@ size_t damn_csr_to_dacsr_workspace_size(void);
 int damn_csr_to_dacsr(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
                       const int32_t *col, int16_t *off_out, damn_fit_info *h_info,
                       void *workspace, size_t ws_bytes, void *stream);
+
+/* Same with 8-bit offsets (DA-CSR-8; the int8 index width of the traffic
+ * lattice of Section 3, Fig. 3): off_out[i] = col[i] - r_i narrowed to
+ * int8, fits iff every offset lies in [-128, 127] (h_info->n_fit counts the
+ * entries in that range).  Same workspace and errors as damn_csr_to_dacsr. */
+int damn_csr_to_dacsr8(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                       const int32_t *col, int8_t *off_out, damn_fit_info *h_info,
+                       void *workspace, size_t ws_bytes, void *stream);
 
 /* Allocation-free variant of damn_csr_to_dacsr (the paper has no counterpart
  * to this entry point).  For callers that cannot allocate device memory: an
@@ -219,15 +228,15 @@ typedef struct {
  * into tiles, the compute mode (chosen from the row-length statistics:
  * DAMN_TILING_ROWS or _ROWS_LONG when rows are uniform inside 32-row groups,
  * DAMN_TILING_SLICES otherwise) and, when idx (col for DAMN_FMT_CSR32, off
- * for DAMN_FMT_DACSR16) is given, the x window of every tile: the tile's
- * sorted distinct columns cut into at most 8 contiguous segments (gaps of up
- * to 32 columns merged), staged in shared memory by the SpMV kernels so that
+ * for DAMN_FMT_DACSR16 / DAMN_FMT_DACSR8) is given, the x window of every
+ * tile: the tile's sorted distinct columns cut into at most 4 contiguous
+ * segments (gaps of up to 32 columns merged), staged in shared memory by the SpMV kernels so that
  * x is not gathered from global memory (the band-window staging of DA-CSR).
  * Tiles whose window does not fit gather x from global memory.  idx may be
  * NULL (no x windows).  Reads rowptr/idx on the device; synchronises.
  * rowptr and idx must stay valid while the plan is used.  The plan owns device
- * memory until damn_plan_destroy.  One plan serves the CSR-32 and DA-CSR-16
- * copies of the same matrix, giving bitwise equal results. */
+ * memory until damn_plan_destroy.  One plan serves the CSR-32, DA-CSR-16 and
+ * DA-CSR-8 copies of the same matrix, giving bitwise equal results. */
 int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
                      int format, const void *idx, int dtype, void *stream, damn_plan **out);
 
@@ -238,9 +247,11 @@ int damn_plan_autotune(damn_plan *plan, int format, const void *idx, const void 
                        const void *x, void *y, void *stream);
 
 /* Pins the plan's tiling: DAMN_TILING_SLICES (tiles balanced on rows +
- * entries, each computed as balanced entry slices), DAMN_TILING_ROWS (224-row
- * tiles, one row per thread; short rows), DAMN_TILING_ROWS_LONG (128-row
- * tiles with larger stages, one row per thread; rows of a few dozen).
+ * entries, each computed as balanced entry slices), DAMN_TILING_ROWS (tiles
+ * of 256 rows with FP64 values, one row per thread, or 512 rows with FP32 /
+ * BF16 values, two rows per thread; short rows), DAMN_TILING_ROWS_LONG
+ * (128-row tiles with larger stages, one row per thread; rows of a few
+ * dozen).
  * Recomputes the x windows; synchronises the legacy default stream. */
 int damn_plan_set_tiling(damn_plan *plan, int tiling);
 
@@ -260,6 +271,12 @@ int damn_spmv_csr32(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *ro
 int damn_spmv_dacsr16(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
                       const int16_t *off, const void *val, int dtype, const void *x, void *y,
                       double alpha, double beta, const damn_plan *plan, void *stream);
+
+/* Same with A in DA-CSR-8 (int8 offsets, from damn_csr_to_dacsr8); for a
+ * given plan bitwise identical to damn_spmv_dacsr16 and damn_spmv_csr32. */
+int damn_spmv_dacsr8(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                     const int8_t *off, const void *val, int dtype, const void *x, void *y,
+                     double alpha, double beta, const damn_plan *plan, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* a6: CG (FP64) and mixed-precision CG with iterative refinement            */

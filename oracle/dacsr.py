@@ -10,7 +10,8 @@ Reading of the 16-bit fit rule: the paper states that a bandwidth below 2^15
 admits 16-bit indices (Example 2, Section 3).  The oracle declares a matrix to
 fit iff every translated index lies in [-32768, 32767], the range a signed
 16-bit integer holds; this differs from "w < 2^15" only when the most negative
-offset is exactly -32768.
+offset is exactly -32768.  The same rule with 8 bits ([-128, 127]) gives
+DA-CSR-8, the int8 index width of the traffic lattice (Section 3, Fig. 3).
 """
 from __future__ import annotations
 
@@ -20,6 +21,8 @@ import numpy as np
 
 INT16_MIN = -(1 << 15)
 INT16_MAX = (1 << 15) - 1
+INT8_MIN = -(1 << 7)
+INT8_MAX = (1 << 7) - 1
 
 
 def entry_rows(nrows: int, rowptr) -> np.ndarray:
@@ -52,21 +55,23 @@ class FitInfo:
     min_off: int     # smallest c - r (0 for an empty matrix)
     max_off: int     # largest c - r (0 for an empty matrix)
     w: int           # Eq. (2) bandwidth, max |c - r|
-    n_fit: int       # entries whose c - r lies in [-32768, 32767]
+    n_fit: int       # entries whose c - r lies in the offset type's range
     n_bad: int       # entries whose column lies outside [0, ncols)
     fits: bool       # every entry fits and every column is in range
 
 
-def fit_check(nrows: int, ncols: int, rowptr, col) -> FitInfo:
+def fit_check(nrows: int, ncols: int, rowptr, col, bits: int = 16) -> FitInfo:
+    """Fit information for offsets of a signed ``bits``-bit type (16 or 8)."""
+    tmin, tmax = (INT16_MIN, INT16_MAX) if bits == 16 else (INT8_MIN, INT8_MAX)
     off = translate(nrows, rowptr, col)
     c = np.asarray(col, dtype=np.int64)
     n_bad = int(np.count_nonzero((c < 0) | (c >= ncols)))
     if off.size == 0:
         return FitInfo(0, 0, 0, 0, n_bad, n_bad == 0)
     lo, hi = int(off.min()), int(off.max())
-    n_fit = int(np.count_nonzero((off >= INT16_MIN) & (off <= INT16_MAX)))
+    n_fit = int(np.count_nonzero((off >= tmin) & (off <= tmax)))
     return FitInfo(lo, hi, int(max(-lo, hi)), n_fit, n_bad,
-                   bool(n_bad == 0 and lo >= INT16_MIN and hi <= INT16_MAX))
+                   bool(n_bad == 0 and lo >= tmin and hi <= tmax))
 
 
 def to_dacsr16(nrows: int, ncols: int, rowptr, col):
@@ -76,3 +81,12 @@ def to_dacsr16(nrows: int, ncols: int, rowptr, col):
     if not info.fits:
         return None, info
     return translate(nrows, rowptr, col).astype(np.int16), info
+
+
+def to_dacsr8(nrows: int, ncols: int, rowptr, col):
+    """CSR -> DA-CSR-8 (int8 offsets).  Returns (off int8 array or None,
+    FitInfo for 8 bits)."""
+    info = fit_check(nrows, ncols, rowptr, col, bits=8)
+    if not info.fits:
+        return None, info
+    return translate(nrows, rowptr, col).astype(np.int8), info

@@ -1,4 +1,4 @@
-// CSR -> DA-CSR-16 translation with the 16-bit fit check (Section 2,
+// CSR -> DA-CSR translation with the 16-bit (or 8-bit) fit check (Section 2,
 // Example 1, Eq. (2)), CSR validation, and round-to-nearest value casts.
 //
 // Each CTA owns a block of kRowsPerBlock rows: it stages their row pointers
@@ -6,7 +6,7 @@
 // and coalesced stores of off, finding each entry's row by binary search in
 // shared memory.  Per-entry work is an int32 subtraction, a narrowing store
 // and min/max/count reductions; the kernel is bound by HBM traffic (4 bytes
-// read + 2 bytes written per entry, plus 4 bytes per row).
+// read + 2 (or 1) bytes written per entry, plus 4 bytes per row).
 #include <algorithm>
 #include <climits>
 #include <mutex>
@@ -70,9 +70,13 @@ __device__ __forceinline__ void block_reduce_fit(int mn, int mx, unsigned long l
   }
 }
 
+// OffT = int16_t (DA-CSR-16) or int8_t (DA-CSR-8): an entry fits when its
+// offset lies in OffT's range.
+template <typename OffT>
 __global__ void __launch_bounds__(kConvThreads)
-k_csr_to_dacsr16(int nrows, int ncols, const int *__restrict__ rowptr, const int *__restrict__ col,
-                 int16_t *__restrict__ off, FitAccum *acc) {
+k_csr_to_dacsr(int nrows, int ncols, const int *__restrict__ rowptr, const int *__restrict__ col,
+               OffT *__restrict__ off, FitAccum *acc) {
+  constexpr int kLo = -(1 << (8 * sizeof(OffT) - 1)), kHi = (1 << (8 * sizeof(OffT) - 1)) - 1;
   __shared__ int rp[kRowsPerBlock + 1];
   const int r0 = blockIdx.x * kRowsPerBlock;
   const int nr = min(kRowsPerBlock, nrows - r0);
@@ -85,10 +89,10 @@ k_csr_to_dacsr16(int nrows, int ncols, const int *__restrict__ rowptr, const int
     const int lr = row_of(rp, nr, k);
     const int c = __ldcs(col + k);
     const int d = c - (r0 + lr);  // |d| < 2^31 since 0 <= r, c < 2^31
-    __stcs(off + k, static_cast<int16_t>(d));
+    off[k] = static_cast<OffT>(d);
     mn = min(mn, d);
     mx = max(mx, d);
-    nf += (d >= -32768 && d <= 32767) ? 1ull : 0ull;
+    nf += (d >= kLo && d <= kHi) ? 1ull : 0ull;
     nb += (c < 0 || c >= ncols) ? 1ull : 0ull;
   }
   block_reduce_fit<kConvThreads>(mn, mx, nf, nb, acc);
@@ -166,23 +170,24 @@ using namespace damn;
 
 extern "C" size_t damn_csr_to_dacsr_workspace_size(void) { return 256; }
 
-extern "C" int damn_csr_to_dacsr(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
-                                 const int32_t *col, int16_t *off_out, damn_fit_info *h_info,
-                                 void *workspace, size_t ws_bytes, void *stream) {
+template <typename OffT>
+static int csr_to_dacsr(const char *fn, int32_t nrows, int32_t ncols, int64_t nnz,
+                        const int32_t *rowptr, const int32_t *col, OffT *off_out,
+                        damn_fit_info *h_info, void *workspace, size_t ws_bytes, void *stream) {
   if (nrows < 0 || ncols < 0 || nnz < 0 || nnz > INT_MAX)
-    return set_error(DAMN_ERR_INVALID_ARG, "damn_csr_to_dacsr: bad sizes");
+    return set_error(DAMN_ERR_INVALID_ARG, "%s: bad sizes", fn);
   if (!h_info || !rowptr || (nnz > 0 && (!col || !off_out)))
-    return set_error(DAMN_ERR_INVALID_ARG, "damn_csr_to_dacsr: NULL pointer");
+    return set_error(DAMN_ERR_INVALID_ARG, "%s: NULL pointer", fn);
   if (!workspace || ws_bytes < damn_csr_to_dacsr_workspace_size() || !aligned16(workspace))
-    return set_error(DAMN_ERR_INVALID_ARG, "damn_csr_to_dacsr: workspace too small or misaligned");
+    return set_error(DAMN_ERR_INVALID_ARG, "%s: workspace too small or misaligned", fn);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   FitAccum *acc = static_cast<FitAccum *>(workspace);
   k_fit_init<<<1, 1, 0, s>>>(acc);
   DAMN_CHECK_LAUNCH("k_fit_init");
   if (nrows > 0) {
     const int blocks = (nrows + kRowsPerBlock - 1) / kRowsPerBlock;
-    k_csr_to_dacsr16<<<blocks, kConvThreads, 0, s>>>(nrows, ncols, rowptr, col, off_out, acc);
-    DAMN_CHECK_LAUNCH("k_csr_to_dacsr16");
+    k_csr_to_dacsr<OffT><<<blocks, kConvThreads, 0, s>>>(nrows, ncols, rowptr, col, off_out, acc);
+    DAMN_CHECK_LAUNCH("k_csr_to_dacsr");
   }
   FitAccum h{};
   DAMN_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -197,10 +202,24 @@ extern "C" int damn_csr_to_dacsr(int32_t nrows, int32_t ncols, int64_t nnz, cons
   h_info->reserved = 0;
   if (!h_info->fits)
     return set_error(DAMN_ERR_NOFIT,
-                     "damn_csr_to_dacsr: %lld of %lld entries do not fit int16 (min %d, max %d), %lld bad columns",
-                     (long long)(nnz - h_info->n_fit), (long long)nnz, h.min_off, h.max_off,
-                     (long long)h.n_bad);
+                     "%s: %lld of %lld entries do not fit int%d (min %d, max %d), %lld bad columns",
+                     fn, (long long)(nnz - h_info->n_fit), (long long)nnz, (int)(8 * sizeof(OffT)),
+                     h.min_off, h.max_off, (long long)h.n_bad);
   return DAMN_OK;
+}
+
+extern "C" int damn_csr_to_dacsr(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                                 const int32_t *col, int16_t *off_out, damn_fit_info *h_info,
+                                 void *workspace, size_t ws_bytes, void *stream) {
+  return csr_to_dacsr<int16_t>("damn_csr_to_dacsr", nrows, ncols, nnz, rowptr, col, off_out,
+                               h_info, workspace, ws_bytes, stream);
+}
+
+extern "C" int damn_csr_to_dacsr8(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                                  const int32_t *col, int8_t *off_out, damn_fit_info *h_info,
+                                  void *workspace, size_t ws_bytes, void *stream) {
+  return csr_to_dacsr<int8_t>("damn_csr_to_dacsr8", nrows, ncols, nnz, rowptr, col, off_out,
+                              h_info, workspace, ws_bytes, stream);
 }
 
 extern "C" size_t damn_validate_csr_workspace_size(void) { return 256; }
@@ -272,7 +291,7 @@ struct __align__(32) FitPartial {
 
 static __device__ __align__(256) FitPartial g_noalloc_fit[kNoAllocMaxBlocks + 1];
 
-// Same per-entry work as k_csr_to_dacsr16; the block's result is written to
+// Same per-entry work as k_csr_to_dacsr<int16_t>; the block's result is written to
 // its own record instead of being combined with atomics.
 __global__ void __launch_bounds__(kConvThreads)
 k_csr_to_dacsr16_part(int nrows, int ncols, const int *__restrict__ rowptr,

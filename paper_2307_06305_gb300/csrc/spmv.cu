@@ -100,6 +100,11 @@ int launch_any(const SpmvParams &p, int dtype, int fmt, int shape, cudaStream_t 
     if (dtype == DAMN_F32) return launch_types<float, int16_t>(p, shape, s, gs);
     return launch_types<__nv_bfloat16, int16_t>(p, shape, s, gs);
   }
+  if (fmt == DAMN_FMT_DACSR8) {
+    if (dtype == DAMN_F64) return launch_types<double, int8_t>(p, shape, s, gs);
+    if (dtype == DAMN_F32) return launch_types<float, int8_t>(p, shape, s, gs);
+    return launch_types<__nv_bfloat16, int8_t>(p, shape, s, gs);
+  }
   if (dtype == DAMN_F64) return launch_types<double, int32_t>(p, shape, s, gs);
   if (dtype == DAMN_F32) return launch_types<float, int32_t>(p, shape, s, gs);
   return launch_types<__nv_bfloat16, int32_t>(p, shape, s, gs);
@@ -208,7 +213,9 @@ k_plan_xseg(int nrows, int ncols, const int *__restrict__ rowptr, const void *id
             const int mid = (lo + hi + 1) >> 1;
             if (rps[mid] <= k) lo = mid; else hi = mid - 1;
           }
-          c = r0 + lo + static_cast<int>(static_cast<const int16_t *>(idx)[k]);
+          c = r0 + lo + (fmt == DAMN_FMT_DACSR8
+                             ? static_cast<int>(static_cast<const int8_t *>(idx)[k])
+                             : static_cast<int>(static_cast<const int16_t *>(idx)[k]));
         }
       }
       keys[i] = c;
@@ -443,6 +450,14 @@ extern "C" int damn_spmv_dacsr16(int32_t nrows, int32_t ncols, int64_t nnz, cons
                     dtype, x, y, alpha, beta, plan, stream);
 }
 
+extern "C" int damn_spmv_dacsr8(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                                const int8_t *off, const void *val, int dtype, const void *x,
+                                void *y, double alpha, double beta, const damn_plan *plan,
+                                void *stream) {
+  return spmv_entry("damn_spmv_dacsr8", DAMN_FMT_DACSR8, nrows, ncols, nnz, rowptr, off, val, dtype,
+                    x, y, alpha, beta, plan, stream);
+}
+
 // ----------------------------------------------------------------------------
 // Plans
 // ----------------------------------------------------------------------------
@@ -519,7 +534,7 @@ extern "C" int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const
     return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_create: bad arguments");
   if (dtype != DAMN_F64 && dtype != DAMN_F32 && dtype != DAMN_BF16)
     return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_create: bad dtype");
-  if (idx && format != DAMN_FMT_CSR32 && format != DAMN_FMT_DACSR16)
+  if (idx && format != DAMN_FMT_CSR32 && format != DAMN_FMT_DACSR16 && format != DAMN_FMT_DACSR8)
     return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_create: bad format");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   damn_plan *pl = new damn_plan();
@@ -570,7 +585,7 @@ extern "C" int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const
 extern "C" int damn_plan_autotune(damn_plan *plan, int format, const void *idx, const void *val,
                                   const void *x, void *y, void *stream) {
   if (!plan) return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_autotune: plan is NULL");
-  if (format != DAMN_FMT_CSR32 && format != DAMN_FMT_DACSR16)
+  if (format != DAMN_FMT_CSR32 && format != DAMN_FMT_DACSR16 && format != DAMN_FMT_DACSR8)
     return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_autotune: bad format");
   int rc = check_spmv_args("damn_plan_autotune", plan->nrows, plan->ncols, plan->nnz, plan->rowptr,
                            idx, val, plan->dtype, x, y, plan);

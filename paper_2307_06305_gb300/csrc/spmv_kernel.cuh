@@ -1,5 +1,5 @@
-// Device side of the SpMV engine: y <- alpha A x + beta y for CSR-32 and
-// DA-CSR-16 (Section 4, Listing 2) with FP64 values, or FP32 / BF16 values
+// Device side of the SpMV engine: y <- alpha A x + beta y for CSR-32,
+// DA-CSR-16 and DA-CSR-8 (Section 4, Listing 2) with FP64 values, or FP32 / BF16 values
 // with FP32 vectors and FP32 accumulation.  Included by spmv.cu only.
 //
 // Design (GB300, sm_103a)
@@ -451,7 +451,7 @@ template <bool PLAIN, typename V, typename I, class C>
 __device__ __noinline__ void rows_general(const SpmvParams &p, unsigned char *smem,
                                           const TileHdr &h, int s, int ctid, double &dsum) {
   using A = typename AccOf<V>::type;
-  constexpr bool DA = sizeof(I) == 2;
+  constexpr bool DA = sizeof(I) < 4;  // int16 / int8 offsets
   TileView<V, I, C> tv;
   tv.init(p, smem, h, s);
   XMap xm;
@@ -480,7 +480,7 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
                                              int ctid, double &dsum) {
   using L = Layout<V, I, C>;
   using A = typename AccOf<V>::type;
-  constexpr bool DA = sizeof(I) == 2;
+  constexpr bool DA = sizeof(I) < 4;  // int16 / int8 offsets
   constexpr int U = C::CAP_NZ / C::TILE_ROWS;
   const int lane = threadIdx.x & 31;
   int j = 0;
@@ -563,7 +563,7 @@ __device__ __forceinline__ void tile_slices(const SpmvParams &p, const TileHdr &
                                             typename AccOf<V>::type *carry,
                                             typename AccOf<V>::type *rowsum, double &dsum) {
   using A = typename AccOf<V>::type;
-  constexpr bool DA = sizeof(I) == 2;
+  constexpr bool DA = sizeof(I) < 4;  // int16 / int8 offsets
   constexpr int G = 8;
   const A *xg = static_cast<const A *>(p.x);
   const int *rp = tv.rp;

@@ -27,7 +27,7 @@ DAMN_ERR_TIMEOUT = -5
 DAMN_ERR_UNSUPPORTED = -6
 
 DAMN_F64, DAMN_F32, DAMN_BF16 = 0, 1, 2
-DAMN_FMT_CSR32, DAMN_FMT_DACSR16 = 0, 1
+DAMN_FMT_CSR32, DAMN_FMT_DACSR16, DAMN_FMT_DACSR8 = 0, 1, 2
 DAMN_TILING_SLICES, DAMN_TILING_ROWS, DAMN_TILING_ROWS_LONG = 0, 1, 2
 
 _DTYPE_CODE = {torch.float64: DAMN_F64, torch.float32: DAMN_F32, torch.bfloat16: DAMN_BF16}
@@ -98,6 +98,8 @@ _sig("damn_selftest_wait_timeout", ctypes.c_int, [I64, P])
 _sig("damn_csr_to_dacsr_workspace_size", SZ, [])
 _sig("damn_csr_to_dacsr", ctypes.c_int,
      [I32, I32, I64, P, P, P, ctypes.POINTER(damn_fit_info), P, SZ, P])
+_sig("damn_csr_to_dacsr8", ctypes.c_int,
+     [I32, I32, I64, P, P, P, ctypes.POINTER(damn_fit_info), P, SZ, P])
 _sig("damn_csr_to_dacsr_noalloc", ctypes.c_int,
      [I32, I32, I64, P, P, P, ctypes.POINTER(damn_fit_info), P])
 _sig("damn_validate_csr_workspace_size", SZ, [])
@@ -113,6 +115,8 @@ _sig("damn_plan_destroy", ctypes.c_int, [P])
 _sig("damn_spmv_csr32", ctypes.c_int,
      [I32, I32, I64, P, P, P, ctypes.c_int, P, P, F64, F64, P, P])
 _sig("damn_spmv_dacsr16", ctypes.c_int,
+     [I32, I32, I64, P, P, P, ctypes.c_int, P, P, F64, F64, P, P])
+_sig("damn_spmv_dacsr8", ctypes.c_int,
      [I32, I32, I64, P, P, P, ctypes.c_int, P, P, F64, F64, P, P])
 
 _OPTIONAL = {}
@@ -230,6 +234,22 @@ def damn_csr_to_dacsr(rowptr: torch.Tensor, col: torch.Tensor, ncols: int, off_o
                             bool(info.fits))
 
 
+def damn_csr_to_dacsr8(rowptr: torch.Tensor, col: torch.Tensor, ncols: int, off_out=None,
+                       stream=None, raise_on_nofit: bool = False):
+    """CSR -> DA-CSR-8: returns (off int8 tensor, FitInfo with the int8 fit)."""
+    nrows = rowptr.numel() - 1
+    nnz = col.numel()
+    if off_out is None:
+        off_out = torch.empty(nnz, dtype=torch.int8, device=col.device)
+    ws = _workspace(_lib.damn_csr_to_dacsr_workspace_size(), col.device)
+    info = damn_fit_info()
+    rc = _lib.damn_csr_to_dacsr8(nrows, int(ncols), nnz, _ptr(rowptr), _ptr(col), _ptr(off_out),
+                                 ctypes.byref(info), _ptr(ws), ws.numel(), _stream(stream))
+    _check(rc, "damn_csr_to_dacsr8", allow=() if raise_on_nofit else (DAMN_ERR_NOFIT,))
+    return off_out, FitInfo(info.min_off, info.max_off, info.w, info.n_fit, info.n_bad,
+                            bool(info.fits))
+
+
 DAMN_NOALLOC_MAX_ROWS = 1048576
 
 
@@ -274,8 +294,8 @@ def damn_cast_values(src: torch.Tensor, dst_dtype: torch.dtype, stream=None) -> 
 
 class Plan:
     """Owns a damn_plan (tiling, compute mode, x windows) for one matrix and
-    one value dtype.  ``idx`` is the column array (int32 col for CSR-32 or
-    int16 off for DA-CSR-16; None: no x windows).  Keep rowptr and idx alive
+    one value dtype.  ``idx`` is the column array (int32 col for CSR-32,
+    int16 / int8 off for DA-CSR-16 / DA-CSR-8; None: no x windows).  Keep rowptr and idx alive
     while the plan is used."""
 
     def __init__(self, rowptr: torch.Tensor, nnz: int, ncols: int, dtype: torch.dtype, idx=None,
@@ -284,7 +304,11 @@ class Plan:
         self.rowptr = rowptr
         self.idx = idx
         self.dtype_code = _DTYPE_CODE[dtype]
-        fmt = DAMN_FMT_DACSR16 if (idx is not None and idx.dtype == torch.int16) else DAMN_FMT_CSR32
+        fmt = DAMN_FMT_CSR32
+        if idx is not None and idx.dtype == torch.int16:
+            fmt = DAMN_FMT_DACSR16
+        elif idx is not None and idx.dtype == torch.int8:
+            fmt = DAMN_FMT_DACSR8
         rc = _lib.damn_plan_create(rowptr.numel() - 1, int(ncols), int(nnz), _ptr(rowptr), fmt,
                                    _ptr(idx), self.dtype_code, _stream(stream),
                                    ctypes.byref(self.handle))
@@ -343,6 +367,17 @@ def damn_spmv_dacsr16(rowptr, off, val, x, y, alpha=1.0, beta=0.0, plan=None, nc
                                 _DTYPE_CODE[val.dtype], _ptr(x), _ptr(y), float(alpha),
                                 float(beta), _plan_handle(plan), _stream(stream))
     _check(rc, "damn_spmv_dacsr16")
+    return y
+
+
+def damn_spmv_dacsr8(rowptr, off, val, x, y, alpha=1.0, beta=0.0, plan=None, ncols=None,
+                     stream=None):
+    nrows = rowptr.numel() - 1
+    ncols = x.numel() if ncols is None else ncols
+    rc = _lib.damn_spmv_dacsr8(nrows, int(ncols), off.numel(), _ptr(rowptr), _ptr(off), _ptr(val),
+                               _DTYPE_CODE[val.dtype], _ptr(x), _ptr(y), float(alpha),
+                               float(beta), _plan_handle(plan), _stream(stream))
+    _check(rc, "damn_spmv_dacsr8")
     return y
 
 

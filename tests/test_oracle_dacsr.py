@@ -94,3 +94,30 @@ def test_workload_fit_rates():
     rp, c, _ = W.laplace3d_7pt(m)
     assert D.bandwidth(m ** 3, rp, c) == m * m
     assert len(c) == 7 * m ** 3 - 6 * m ** 2
+
+
+@pytest.mark.parametrize("extreme,fits", [(127, True), (-127, True), (-128, True),
+                                          (128, False), (-129, False)])
+def test_int8_boundary(extreme, fits):
+    """DA-CSR-8: the same rule over [-128, 127]."""
+    n = 400
+    r = 200
+    rows = np.append(np.arange(n), r)
+    cols = np.append(np.arange(n), r + extreme)
+    rp, c, _ = W.from_coo(n, rows, cols)
+    off, info = D.to_dacsr8(n, n, rp, c)
+    assert info.fits == fits
+    assert info.w == abs(extreme)
+    assert info.n_fit == n + (1 if fits else 0)
+    if fits:
+        assert off.dtype == np.int8
+        assert int(off.min()) == min(0, extreme) and int(off.max()) == max(0, extreme)
+        assert np.array_equal(D.untranslate(n, rp, off), c)
+
+
+def test_int8_fit_of_grids():
+    # 2-D 5-point Laplacian: w = m, so DA-CSR-8 holds up to m = 127
+    for m, fits in ((127, True), (128, False)):
+        rp, c, _ = W.laplace2d_5pt(m)
+        assert D.fit_check(m * m, m * m, rp, c, bits=8).fits == fits
+        assert D.fit_check(m * m, m * m, rp, c, bits=16).fits
