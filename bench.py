@@ -24,9 +24,14 @@ none of them inside the headline's timed region):
   * ``solvers``: 160^3 27-point stencil, time to a true relative residual of
     1e-10 for FP64 CG and for CG with FP64 refinement around FP32 / BF16
     DA-CSR-16 inner solves;
+  * ``solvers_perturbed``: the same with a symmetric N(0, 0.01^2)
+    perturbation of the off-diagonals (values no longer exact in FP32 /
+    BF16), with the low-precision SpMV error per dtype;
   * ``batched``: 512 random banded matrices, k in {1, 4, 16} right-hand
     sides, FP64 / FP32: one persistent launch (direct and graph replay) vs
     512 per-matrix launches (eager and graph-captured);
+  * ``da8``: DA-CSR-8 (int8 offsets) vs DA-CSR-16 vs CSR-32 on a 2-D
+    Laplacian whose half-bandwidth (127) fits int8, FP64 and FP32 values;
   * ``small``: the 64x64 5-point Laplacian, SpMV time per call under graph
     replay (launch / latency bound, in L2).
 
@@ -284,13 +289,18 @@ def section_conversion_rcm(D, torch, dev, reps):
     return out
 
 
-def section_solvers(D, torch, dev, reps):
+def section_solvers(D, torch, dev, reps, perturb=False):
     """a5/a6: FP64 CG vs CG-IR (FP32 / BF16 inner values) on the 160^3
-    27-point stencil, time to a true relative residual of 1e-10."""
+    27-point stencil, time to a true relative residual of 1e-10.  With
+    perturb, the off-diagonals get a symmetric N(0, 0.01^2) perturbation
+    (still SPD), so FP32 / BF16 value quantisation is not exact, and the
+    low-precision SpMV error against the FP64 SpMV is reported per dtype."""
     import workloads as W
     m = 160
     rp, col, val = W.stencil27(m)
     n, nnz = len(rp) - 1, len(col)
+    if perturb:
+        val = W.perturb_symmetric(n, rp, col, val, sigma=0.01)
     t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
     off, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
     del t_col
@@ -319,7 +329,15 @@ def section_solvers(D, torch, dev, reps):
         "cg_ir_bf16": lambda: D.damn_cg_ir(t_rp, off, t_val, v16, b, x, 1e-10, 1e-2, 200, 60,
                                            plan64=p64, plan_low=p16, workspace=ws_ir),
     }
-    out = {"workload": "stencil27_160^3_cg_to_1e-10", "n": n, "nnz": nnz}
+    out = {"workload": "stencil27_160^3_cg_to_1e-10" + ("_perturbed_0.01" if perturb else ""),
+           "n": n, "nnz": nnz}
+    # low-precision SpMV error against the FP64 SpMV, per dtype (x = x*)
+    y64 = torch.empty(n, dtype=torch.float64, device=dev)
+    D.damn_spmv_dacsr16(t_rp, off, t_val, xs, y64, plan=p64)
+    for name, vl, pl in (("f32", v32, p32), ("bf16", v16, p16)):
+        D.damn_spmv_dacsr16(t_rp, off, vl, x32, y32, plan=pl)
+        err = float((y32.double() - y64).abs().max() / y64.abs().max())
+        out[f"spmv_{name}_max_rel_err_vs_f64"] = float(f"{err:.3e}")
     stream = torch.cuda.current_stream()
     for name, fn in runs.items():
         ts, res = [], None
@@ -409,6 +427,48 @@ def section_batched(D, torch, dev, reps):
     return out
 
 
+def section_da8(D, torch, dev, reps):
+    """DA-CSR-8 vs DA-CSR-16 vs CSR-32 on a matrix whose bandwidth fits int8:
+    2-D 5-point Laplacian, 131072 lines of 127 points (w = 127), one copy of
+    > 1 GB (larger than L2), FP64 and FP32 values."""
+    import workloads as W
+    mx, my = 127, 131072
+    rp, col, val = W.laplace2d_5pt_rect(mx, my)
+    n, nnz = len(rp) - 1, len(col)
+    t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
+    del rp, col
+    off8, fi8 = D.damn_csr_to_dacsr8(t_rp, t_col, n, raise_on_nofit=True)
+    off16, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
+    t_val = torch.from_numpy(val).to(dev)
+    del val
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.seed_for(3, 8))
+    out = {"workload": f"laplace2d_5pt_{mx}x{my}", "n": n, "nnz": nnz, "w": int(fi8.w)}
+    for name, dt, vb, xb in (("f64", torch.float64, 8, 8), ("f32", torch.float32, 4, 4)):
+        vals = t_val if dt == torch.float64 else D.damn_cast_values(t_val, torch.float32)
+        x = torch.rand(n, generator=gen, device=dev, dtype=torch.float64).to(dt) * 2 - 1
+        y = torch.empty(n, dtype=dt, device=dev)
+        plan = D.Plan(t_rp, nnz, n, dt, idx=off8)
+        res = {}
+        for fmt, fn, idx, ib in (("da8", D.damn_spmv_dacsr8, off8, 1),
+                                 ("da16", D.damn_spmv_dacsr16, off16, 2),
+                                 ("csr32", D.damn_spmv_csr32, t_col, 4)):
+            for _ in range(3):
+                fn(t_rp, idx, vals, x, y, plan=plan)
+            t, _ = _event_time(torch, lambda: [fn(t_rp, idx, vals, x, y, plan=plan) for _ in range(10)],
+                               max(3, reps // 2))
+            t /= 10
+            b = spmv_bytes(n, nnz, ib, vb, xb)
+            res[fmt] = {"us": round(t * 1e6, 1), "gbs": round(b / t / 1e9, 1), "bytes": b}
+        res["speedup_da8_over_da16"] = round(res["da16"]["us"] / res["da8"]["us"], 4)
+        res["speedup_da8_over_csr32"] = round(res["csr32"]["us"] / res["da8"]["us"], 4)
+        res["model_da8_over_csr32"] = round(res["csr32"]["bytes"] / res["da8"]["bytes"], 4)
+        res["tiling"] = plan.describe()["tiling"]
+        out[name] = res
+        del plan, vals, x, y
+    return out
+
+
 def section_small(D, torch, dev, reps):
     """Config 1 size (64x64 5-point Laplacian, in L2): time per SpMV under
     graph replay of 1000 calls."""
@@ -445,7 +505,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
-    ap.add_argument("--sections", default="conversion,solvers,batched,small",
+    ap.add_argument("--sections", default="conversion,solvers,solvers_perturbed,batched,da8,small",
                     help="comma list of secondary sections to run after the headline ('' for none)")
     ap.add_argument("--section-reps", type=int, default=10)
     ap.add_argument("--tiling", default="auto", choices=["auto", "rows", "rows_long", "slices"],
@@ -602,7 +662,8 @@ def main():
     }
     secs = [t for t in args.sections.split(",") if t]
     fns = {"conversion": section_conversion_rcm, "solvers": section_solvers,
-           "batched": section_batched, "small": section_small}
+           "solvers_perturbed": lambda *a: section_solvers(*a, perturb=True),
+           "batched": section_batched, "da8": section_da8, "small": section_small}
     for name in secs:
         t0 = time.perf_counter()
         res = fns[name](D, torch, dev, args.section_reps)

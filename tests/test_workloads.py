@@ -73,3 +73,19 @@ def test_batch_banded():
         assert D.bandwidth(n, rp, c) <= 4096
         lens = np.diff(rp)
         assert lens.min() >= 1 and lens.max() <= 40
+
+
+def test_perturb_symmetric_keeps_symmetry_and_dominance():
+    m = 10
+    rp, col, val = W.stencil27(m)
+    n = m ** 3
+    pv = W.perturb_symmetric(n, rp, col, val, sigma=0.01)
+    import scipy.sparse as sp
+    A = sp.csr_matrix((pv, col, rp), shape=(n, n))
+    assert abs(A - A.T).max() == 0.0
+    d = A.diagonal()
+    assert np.array_equal(d, np.full(n, 26.5))
+    off = np.asarray(abs(A).sum(axis=1)).ravel() - np.abs(d)
+    assert np.all(off < d)                          # strictly diagonally dominant: SPD
+    delta = (pv - val)[(pv - val) != 0]
+    assert 0.008 < delta.std() < 0.012 and abs(delta.mean()) < 0.002

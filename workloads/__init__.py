@@ -132,6 +132,14 @@ def laplace2d_5pt(m: int = 64):
     return _grid_stencil((m, m), offs, vals)
 
 
+def laplace2d_5pt_rect(mx: int, my: int):
+    """2-D 5-point Laplacian on a grid of my lines of mx points, natural
+    (row-major) order: half-bandwidth mx."""
+    offs = [(-1, 0), (0, -1), (0, 0), (0, 1), (1, 0)]
+    vals = [-1.0, -1.0, 4.0, -1.0, -1.0]
+    return _grid_stencil((my, mx), offs, vals)
+
+
 def _chunked_stencil(m: int, offsets, values, labels=None, chunk_planes: int = 8):
     """3-D stencil assembled plane block by plane block (bounded memory)."""
     if labels is None:
@@ -195,6 +203,39 @@ def stencil27(m: int = 160, diag: float = 26.5, off: float = -1.0):
     offs = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
     vals = [diag if o == (0, 0, 0) else off for o in offs]
     return _grid_stencil_natural_3d(m, offs, vals)
+
+
+def _splitmix64(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser (Steele, Lea & Flood 2014) on uint64 counters."""
+    z = (z + np.uint64(0x9E3779B97F4A7C15)) & np.uint64(0xFFFFFFFFFFFFFFFF)
+    z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & np.uint64(0xFFFFFFFFFFFFFFFF)
+    z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & np.uint64(0xFFFFFFFFFFFFFFFF)
+    return z ^ (z >> np.uint64(31))
+
+
+def perturb_symmetric(n: int, rowptr, col, val, sigma: float = 0.01, seed: int | None = None,
+                      chunk: int = 1 << 24):
+    """Adds N(0, sigma^2) to every off-diagonal entry, the same value to
+    (i, j) and (j, i): the normal is drawn (Box-Muller) from a counter-based
+    hash of the unordered pair, so no pairing pass is needed.  Returns new
+    values; A stays symmetric."""
+    if seed is None:
+        seed = seed_for(4, 7)
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    out = np.array(val, dtype=np.float64, copy=True)
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    s = np.uint64(seed & 0xFFFFFFFFFFFFFFFF)
+    for a in range(0, len(col), chunk):
+        r, c = rows[a:a + chunk], col[a:a + chunk]
+        key = (np.minimum(r, c) * np.int64(n) + np.maximum(r, c)).astype(np.uint64)
+        h1 = _splitmix64(key ^ s)
+        h2 = _splitmix64(h1)
+        u1 = ((h1 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53   # (0, 1]
+        u2 = (h2 >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+        g = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+        out[a:a + chunk] += np.where(r != c, sigma * g, 0.0)
+    return out
 
 
 # ----------------------------------------------------------------------------
