@@ -607,25 +607,71 @@ def main():
         def step_m(i, vals=vals, pl=pl, x32=x32, y32=y32):
             c = i % NCOPY
             D.damn_spmv_dacsr16(t_rp[c], t_off[c], vals[c], x32, y32, plan=pl[c])
+        def step_mc(i, vals=vals, pl=pl, x32=x32, y32=y32):
+            c = i % NCOPY
+            D.damn_spmv_csr32(t_rp[c], t_col[c], vals[c], x32, y32, plan=pl[c])
         tm = timed(step_m, args.steps, args.warmup) / args.steps
+        tc = timed(step_mc, args.steps, args.warmup) / args.steps
         bm = spmv_bytes(n, nnz, 2, vb, 4)
+        bc = spmv_bytes(n, nnz, 4, vb, 4)
         mixed[name] = {"gbs": round(bm / tm / 1e9, 1), "us": round(tm * 1e6, 2),
-                       "bytes": bm}
+                       "bytes": bm, "csr32_us": round(tc * 1e6, 2),
+                       "csr32_gbs": round(bc / tc / 1e9, 1),
+                       "speedup_da16_over_csr32": round(tc / tm, 4),
+                       "model_speedup": round(bc / bm, 4)}
         del vals, pl
 
-    # end to end through the public API: pinned host x -> device, SpMV, y -> host
-    hx = torch.from_numpy(x).pin_memory()
-    hy = torch.empty(n, dtype=torch.float64).pin_memory()
-    dx = torch.empty(n, dtype=torch.float64, device=dev)
+    # end to end through the public API: every step uploads its x from pinned
+    # host memory, runs the SpMV and reads its y back.  Steps are pipelined
+    # over three streams (upload of step i+1 and download of step i-1 overlap
+    # the SpMV of step i), with two x and two y buffers ordered by events.
+    hx = [torch.from_numpy(x).pin_memory() for _ in range(2)]
+    hy = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(2)]
+    dx = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
+    dy = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_c = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
 
-    def step_e2e(i):
-        c = i % NCOPY
-        dx.copy_(hx, non_blocking=True)
-        D.damn_spmv_dacsr16(t_rp[c], t_off[c], t_val[c], dx, y, plan=plans[c])
-        hy.copy_(y, non_blocking=True)
+    def run_e2e(nsteps):
+        for i in range(nsteps):
+            b, c = i % 2, i % NCOPY
+            if i >= 2:
+                s_in.wait_event(ev_c[b])          # SpMV(i-2) has read dx[b]
+            with torch.cuda.stream(s_in):
+                dx[b].copy_(hx[b], non_blocking=True)
+            ev_in[b].record(s_in)
+            stream.wait_event(ev_in[b])
+            if i >= 2:
+                stream.wait_event(ev_out[b])      # download(i-2) has read dy[b]
+            D.damn_spmv_dacsr16(t_rp[c], t_off[c], t_val[c], dx[b], dy[b], plan=plans[c],
+                                stream=stream)
+            ev_c[b].record(stream)
+            s_out.wait_event(ev_c[b])
+            with torch.cuda.stream(s_out):
+                hy[b].copy_(dy[b], non_blocking=True)
+            ev_out[b].record(s_out)
+        stream.wait_stream(s_in)
+        stream.wait_stream(s_out)
 
     e2e_steps = max(10, args.steps // 4)
-    t_e2e = timed(step_e2e, e2e_steps, min(args.warmup, 5)) / e2e_steps
+    run_e2e(min(args.warmup, 5))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s_in.wait_stream(stream)
+    run_e2e(e2e_steps)
+    e1.record(stream)
+    barrier()
+    t_e2e = e0.elapsed_time(e1) * 1e-3 / e2e_steps
+    if dist is not None:
+        tt = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    if not torch.equal(torch.from_numpy(hy[(e2e_steps - 1) % 2].numpy()).to(dev), dy[(e2e_steps - 1) % 2]):
+        raise RuntimeError("e2e: downloaded y differs from the device result")
     e2e_value = world * b_da / t_e2e / 1e9
     clk.__exit__(None, None, None)
 
@@ -656,7 +702,8 @@ def main():
         "da16_us": round(per_step_da * 1e6, 2),
         "mixed_precision_spmv": mixed,
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 8 * n,
-                "d2h_bytes_per_step": 8 * n, "us_per_step": round(t_e2e * 1e6, 2)},
+                "d2h_bytes_per_step": 8 * n, "us_per_step": round(t_e2e * 1e6, 2),
+                "pipelined": "upload / SpMV / download of consecutive steps overlap on 3 streams"},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
