@@ -32,6 +32,8 @@ none of them inside the headline's timed region):
     512 per-matrix launches (eager and graph-captured);
   * ``da8``: DA-CSR-8 (int8 offsets) vs DA-CSR-16 vs CSR-32 on a 2-D
     Laplacian whose half-bandwidth (127) fits int8, FP64 and FP32 values;
+  * ``dabsr``: DA-BSR-16 vs BSR-32 (diagonal addressing of the block
+    pattern) on a 96^3 grid with dense 3 x 3 blocks, FP64 and FP32 values;
   * ``small``: the 64x64 5-point Laplacian, SpMV time per call under graph
     replay (launch / latency bound, in L2).
 
@@ -469,6 +471,43 @@ def section_da8(D, torch, dev, reps):
     return out
 
 
+def section_dabsr(D, torch, dev, reps):
+    """DA-BSR-16 vs BSR-32: the 3-D 7-point block pattern on a 96^3 grid with
+    dense 3 x 3 blocks (3 unknowns per point), FP64 and FP32 values."""
+    import workloads as W
+    m, b = 96, 3
+    nbr, browptr, bcol, bval = W.block_stencil3d(m, b)
+    nblk = len(bcol)
+    t_bp, t_bc = torch.from_numpy(browptr).to(dev), torch.from_numpy(bcol).to(dev)
+    off16, fi = D.damn_csr_to_dacsr(t_bp, t_bc, nbr, raise_on_nofit=True)
+    t_val = torch.from_numpy(bval.reshape(-1)).to(dev)
+    del bval
+    n = nbr * b
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.seed_for(6, 9))
+    out = {"workload": f"block_stencil3d_{m}^3_b{b}", "block_rows": nbr, "blocks": nblk,
+           "nnz": nblk * b * b, "block_w": int(fi.w)}
+    for name, dt, vb in (("f64", torch.float64, 8), ("f32", torch.float32, 4)):
+        vals = t_val if dt == torch.float64 else D.damn_cast_values(t_val, torch.float32)
+        x = (torch.rand(n, generator=gen, device=dev, dtype=torch.float64) * 2 - 1).to(dt)
+        y = torch.empty(n, dtype=dt, device=dev)
+        res = {}
+        for fmt, fn, idx, ib in (("dabsr16", D.damn_spmv_dabsr16, off16, 2),
+                                 ("bsr32", D.damn_spmv_bsr32, t_bc, 4)):
+            for _ in range(3):
+                fn(t_bp, idx, vals, b, x, y)
+            t, _ = _event_time(torch, lambda: [fn(t_bp, idx, vals, b, x, y) for _ in range(10)],
+                               max(3, reps // 2))
+            t /= 10
+            bytes_ = (nbr + 1) * 4 + nblk * (ib + b * b * vb) + 2 * n * vb
+            res[fmt] = {"us": round(t * 1e6, 1), "gbs": round(bytes_ / t / 1e9, 1), "bytes": bytes_}
+        res["speedup_dabsr16_over_bsr32"] = round(res["bsr32"]["us"] / res["dabsr16"]["us"], 4)
+        res["model_speedup"] = round(res["bsr32"]["bytes"] / res["dabsr16"]["bytes"], 4)
+        out[name] = res
+        del vals, x, y
+    return out
+
+
 def section_small(D, torch, dev, reps):
     """Config 1 size (64x64 5-point Laplacian, in L2): time per SpMV under
     graph replay of 1000 calls."""
@@ -505,7 +544,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
-    ap.add_argument("--sections", default="conversion,solvers,solvers_perturbed,batched,da8,small",
+    ap.add_argument("--sections",
+                    default="conversion,solvers,solvers_perturbed,batched,da8,dabsr,small",
                     help="comma list of secondary sections to run after the headline ('' for none)")
     ap.add_argument("--section-reps", type=int, default=10)
     ap.add_argument("--tiling", default="auto", choices=["auto", "rows", "rows_long", "slices"],
@@ -710,7 +750,8 @@ def main():
     secs = [t for t in args.sections.split(",") if t]
     fns = {"conversion": section_conversion_rcm, "solvers": section_solvers,
            "solvers_perturbed": lambda *a: section_solvers(*a, perturb=True),
-           "batched": section_batched, "da8": section_da8, "small": section_small}
+           "batched": section_batched, "da8": section_da8, "dabsr": section_dabsr,
+           "small": section_small}
     for name in secs:
         t0 = time.perf_counter()
         res = fns[name](D, torch, dev, args.section_reps)

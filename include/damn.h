@@ -279,6 +279,31 @@ int damn_spmv_dacsr8(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *r
                      double alpha, double beta, const damn_plan *plan, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* DA-BSR: diagonal addressing of block CSR (the technique applied to BSR,   */
+/* Section 1)                                                                */
+/* ------------------------------------------------------------------------ */
+/* y <- alpha A x + beta y with A in block CSR: nbr x nbc blocks of b x b
+ * (b in {1, 2, 3, 4, 6, 8}), browptr int32[nbr+1] over the nblk stored
+ * blocks, per block its column (bsr32: absolute block column, int32) or its
+ * offset from the block diagonal (dabsr16 / dabsr8: C - R as int16 / int8,
+ * produced by damn_csr_to_dacsr / damn_csr_to_dacsr8 applied to the block
+ * pattern (nbr, nbc, nblk, browptr, bcol)), and b*b values per block,
+ * row-major inside the block (val[nblk][b][b]).  x has nbc*b entries, y
+ * nbr*b.  Scalar row R*b + i accumulates, over the row's blocks in stored
+ * order and j = 0..b-1, val[k][i][j] * x[C_k*b + j] with FMA; the three
+ * variants give bitwise equal results.  dtype as for damn_spmv_dacsr16.
+ * beta == 0: y is output only.  Asynchronous. */
+int damn_spmv_bsr32(int32_t nbr, int32_t nbc, int64_t nblk, int32_t b, const int32_t *browptr,
+                    const int32_t *bcol, const void *val, int dtype, const void *x, void *y,
+                    double alpha, double beta, void *stream);
+int damn_spmv_dabsr16(int32_t nbr, int32_t nbc, int64_t nblk, int32_t b, const int32_t *browptr,
+                      const int16_t *boff, const void *val, int dtype, const void *x, void *y,
+                      double alpha, double beta, void *stream);
+int damn_spmv_dabsr8(int32_t nbr, int32_t nbc, int64_t nblk, int32_t b, const int32_t *browptr,
+                     const int8_t *boff, const void *val, int dtype, const void *x, void *y,
+                     double alpha, double beta, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* a6: CG (FP64) and mixed-precision CG with iterative refinement            */
 /* ------------------------------------------------------------------------ */
 typedef struct {

@@ -23,6 +23,8 @@ order and notation so that a reader can check it by eye:
   multi-right-hand-side product.
 * ``cg``       -- FP64 conjugate gradients and mixed-precision iterative
   refinement around a low-precision CG.
+* ``bsr``      -- block CSR and its diagonally-addressed form (DA-BSR),
+  expanded to scalar CSR so the SpMV definitions above apply.
 * ``spmv_listing2.c`` -- a plain C restatement of Listing 2 (CSR-32 and
   DA-CSR-16, FP64, OpenMP row partition), used as the timed CPU baseline.
 

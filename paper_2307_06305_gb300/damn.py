@@ -118,6 +118,8 @@ _sig("damn_spmv_dacsr16", ctypes.c_int,
      [I32, I32, I64, P, P, P, ctypes.c_int, P, P, F64, F64, P, P])
 _sig("damn_spmv_dacsr8", ctypes.c_int,
      [I32, I32, I64, P, P, P, ctypes.c_int, P, P, F64, F64, P, P])
+for _n in ("damn_spmv_bsr32", "damn_spmv_dabsr16", "damn_spmv_dabsr8"):
+    _sig(_n, ctypes.c_int, [I32, I32, I64, I32, P, P, P, ctypes.c_int, P, P, F64, F64, P])
 
 _OPTIONAL = {}
 
@@ -379,6 +381,31 @@ def damn_spmv_dacsr8(rowptr, off, val, x, y, alpha=1.0, beta=0.0, plan=None, nco
                                float(beta), _plan_handle(plan), _stream(stream))
     _check(rc, "damn_spmv_dacsr8")
     return y
+
+
+def _bsr_call(name, browptr, bidx, val, b, x, y, alpha, beta, nbc, stream):
+    nbr = browptr.numel() - 1
+    nbc = (x.numel() // b) if nbc is None else nbc
+    rc = getattr(_lib, name)(nbr, int(nbc), bidx.numel(), int(b), _ptr(browptr), _ptr(bidx),
+                             _ptr(val), _DTYPE_CODE[val.dtype], _ptr(x), _ptr(y), float(alpha),
+                             float(beta), _stream(stream))
+    _check(rc, name)
+    return y
+
+
+def damn_spmv_bsr32(browptr, bcol, val, b, x, y, alpha=1.0, beta=0.0, nbc=None, stream=None):
+    """Block CSR SpMV; val is [nblk * b * b] (blocks row-major)."""
+    return _bsr_call("damn_spmv_bsr32", browptr, bcol, val, b, x, y, alpha, beta, nbc, stream)
+
+
+def damn_spmv_dabsr16(browptr, boff, val, b, x, y, alpha=1.0, beta=0.0, nbc=None, stream=None):
+    """DA-BSR SpMV with int16 block offsets (from damn_csr_to_dacsr on the block pattern)."""
+    return _bsr_call("damn_spmv_dabsr16", browptr, boff, val, b, x, y, alpha, beta, nbc, stream)
+
+
+def damn_spmv_dabsr8(browptr, boff, val, b, x, y, alpha=1.0, beta=0.0, nbc=None, stream=None):
+    """DA-BSR SpMV with int8 block offsets (from damn_csr_to_dacsr8 on the block pattern)."""
+    return _bsr_call("damn_spmv_dabsr8", browptr, boff, val, b, x, y, alpha, beta, nbc, stream)
 
 
 # ----------------------------------------------------------------------------

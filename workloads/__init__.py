@@ -346,3 +346,21 @@ def from_coo(n_rows: int, rows, cols, vals=None):
     rowptr = np.zeros(n_rows + 1, dtype=np.int64)
     np.cumsum(counts, out=rowptr[1:])
     return rowptr.astype(np.int32), cols.astype(np.int32), vals
+
+
+def block_stencil3d(m: int, b: int, rng: np.random.Generator | None = None):
+    """Block sparse matrix with the pattern of the 3-D 7-point stencil on an
+    m^3 grid (natural order) and dense b x b blocks (b unknowns per grid
+    point, as in 3-D elasticity): block values N(0, 1), plus 2 b on the
+    diagonal of each diagonal block.  Returns (nbr, browptr, bcol,
+    bval[nblk, b, b])."""
+    if rng is None:
+        rng = rng_for(6, b)
+    rp, col, _ = laplace3d_7pt(m)
+    nbr = m ** 3
+    nblk = len(col)
+    bval = rng.standard_normal((nblk, b, b))
+    rows = np.repeat(np.arange(nbr, dtype=np.int64), np.diff(rp.astype(np.int64)))
+    diag = rows == col
+    bval[diag] += 2.0 * b * np.eye(b)[None, :, :]
+    return nbr, rp, col, bval
