@@ -34,6 +34,7 @@ none of them inside the headline's timed region):
     Laplacian whose half-bandwidth (127) fits int8, FP64 and FP32 values;
   * ``dabsr``: DA-BSR-16 vs BSR-32 (diagonal addressing of the block
     pattern) on a 96^3 grid with dense 3 x 3 blocks, FP64 and FP32 values;
+  * ``dacoo``: DA-COO-16 vs COO-32 on the 128^3 Laplacian;
   * ``small``: the 64x64 5-point Laplacian, SpMV time per call under graph
     replay (launch / latency bound, in L2).
 
@@ -508,6 +509,40 @@ def section_dabsr(D, torch, dev, reps):
     return out
 
 
+def section_dacoo(D, torch, dev, reps):
+    """DA-COO-16 vs COO-32 on the 128^3 7-point Laplacian (row vector int32,
+    column vector as int16 offsets or int32 columns), FP64 and FP32 values."""
+    import workloads as W
+    rp, col, val = W.laplace3d_7pt(GRID)
+    n, nnz = len(rp) - 1, len(col)
+    row = np.repeat(np.arange(n, dtype=np.int32), np.diff(rp))
+    t_row, t_col = torch.from_numpy(row).to(dev), torch.from_numpy(col).to(dev)
+    t_rp = torch.from_numpy(rp).to(dev)
+    off, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
+    t_val = torch.from_numpy(val).to(dev)
+    out = {"workload": "laplace3d_7pt_128^3_coo", "n": n, "nnz": nnz}
+    for name, dt, vb in (("f64", torch.float64, 8), ("f32", torch.float32, 4)):
+        vals = t_val if dt == torch.float64 else D.damn_cast_values(t_val, torch.float32)
+        x = torch.from_numpy(W.uniform_vector(n, W.rng_for(2, 0))).to(dev).to(dt)
+        y = torch.empty(n, dtype=dt, device=dev)
+        ws = D._workspace(D._fn("damn_coo_workspace_size")(nnz, D._DTYPE_CODE[dt]), dev)
+        res = {}
+        for fmt, fn, idx, ib in (("dacoo16", D.damn_spmv_dacoo16, off, 2),
+                                 ("coo32", D.damn_spmv_coo32, t_col, 4)):
+            for _ in range(3):
+                fn(n, t_row, idx, vals, x, y, workspace=ws)
+            t, _ = _event_time(torch, lambda: [fn(n, t_row, idx, vals, x, y, workspace=ws)
+                                               for _ in range(10)], max(3, reps // 2))
+            t /= 10
+            b = nnz * (4 + ib + vb) + 2 * n * vb
+            res[fmt] = {"us": round(t * 1e6, 1), "gbs": round(b / t / 1e9, 1), "bytes": b}
+        res["speedup_dacoo16_over_coo32"] = round(res["coo32"]["us"] / res["dacoo16"]["us"], 4)
+        res["model_speedup"] = round(res["coo32"]["bytes"] / res["dacoo16"]["bytes"], 4)
+        out[name] = res
+        del vals, x, y, ws
+    return out
+
+
 def section_small(D, torch, dev, reps):
     """Config 1 size (64x64 5-point Laplacian, in L2): time per SpMV under
     graph replay of 1000 calls."""
@@ -545,7 +580,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--sections",
-                    default="conversion,solvers,solvers_perturbed,batched,da8,dabsr,small",
+                    default="conversion,solvers,solvers_perturbed,batched,da8,dabsr,dacoo,small",
                     help="comma list of secondary sections to run after the headline ('' for none)")
     ap.add_argument("--section-reps", type=int, default=10)
     ap.add_argument("--tiling", default="auto", choices=["auto", "rows", "rows_long", "slices"],
@@ -751,6 +786,7 @@ def main():
     fns = {"conversion": section_conversion_rcm, "solvers": section_solvers,
            "solvers_perturbed": lambda *a: section_solvers(*a, perturb=True),
            "batched": section_batched, "da8": section_da8, "dabsr": section_dabsr,
+           "dacoo": section_dacoo,
            "small": section_small}
     for name in secs:
         t0 = time.perf_counter()

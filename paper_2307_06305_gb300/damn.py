@@ -118,6 +118,9 @@ _sig("damn_spmv_dacsr16", ctypes.c_int,
      [I32, I32, I64, P, P, P, ctypes.c_int, P, P, F64, F64, P, P])
 _sig("damn_spmv_dacsr8", ctypes.c_int,
      [I32, I32, I64, P, P, P, ctypes.c_int, P, P, F64, F64, P, P])
+_sig("damn_coo_workspace_size", SZ, [I64, ctypes.c_int])
+for _n in ("damn_spmv_coo32", "damn_spmv_dacoo16"):
+    _sig(_n, ctypes.c_int, [I32, I32, I64, P, P, P, ctypes.c_int, P, P, F64, F64, P, SZ, P])
 for _n in ("damn_spmv_bsr32", "damn_spmv_dabsr16", "damn_spmv_dabsr8"):
     _sig(_n, ctypes.c_int, [I32, I32, I64, I32, P, P, P, ctypes.c_int, P, P, F64, F64, P])
 
@@ -406,6 +409,32 @@ def damn_spmv_dabsr16(browptr, boff, val, b, x, y, alpha=1.0, beta=0.0, nbc=None
 def damn_spmv_dabsr8(browptr, boff, val, b, x, y, alpha=1.0, beta=0.0, nbc=None, stream=None):
     """DA-BSR SpMV with int8 block offsets (from damn_csr_to_dacsr8 on the block pattern)."""
     return _bsr_call("damn_spmv_dabsr8", browptr, boff, val, b, x, y, alpha, beta, nbc, stream)
+
+
+def _coo_call(name, nrows, row, idx, val, x, y, alpha, beta, ncols, stream, workspace):
+    ncols = x.numel() if ncols is None else ncols
+    dt = _DTYPE_CODE[val.dtype]
+    ws = workspace if workspace is not None else \
+        _workspace(_lib.damn_coo_workspace_size(idx.numel(), dt), y.device)
+    rc = getattr(_lib, name)(int(nrows), int(ncols), idx.numel(), _ptr(row), _ptr(idx), _ptr(val),
+                             dt, _ptr(x), _ptr(y), float(alpha), float(beta), _ptr(ws), ws.numel(),
+                             _stream(stream))
+    _check(rc, name)
+    return y
+
+
+def damn_spmv_coo32(nrows, row, col, val, x, y, alpha=1.0, beta=0.0, ncols=None, stream=None,
+                    workspace=None):
+    """COO SpMV, entries sorted by row."""
+    return _coo_call("damn_spmv_coo32", nrows, row, col, val, x, y, alpha, beta, ncols, stream,
+                     workspace)
+
+
+def damn_spmv_dacoo16(nrows, row, off, val, x, y, alpha=1.0, beta=0.0, ncols=None, stream=None,
+                      workspace=None):
+    """DA-COO SpMV: int16 offsets c - r instead of columns, entries sorted by row."""
+    return _coo_call("damn_spmv_dacoo16", nrows, row, off, val, x, y, alpha, beta, ncols, stream,
+                     workspace)
 
 
 # ----------------------------------------------------------------------------
