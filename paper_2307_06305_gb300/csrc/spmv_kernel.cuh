@@ -107,15 +107,18 @@ struct SpmvParams {
   unsigned long long timeout_ns;
 };
 
-// NT consumer threads; rows mode: tiles of TILE_ROWS = RPT * NT rows, each
-// thread computing RPT of them.  CAP_NZ / CAP_ROWS / XCAP: capacity of one
+// NT consumer threads; rows mode: tiles of TILE_ROWS = RPT * NT / E rows,
+// E lanes sharing each row (entries e, e + E, ... per lane, partial sums
+// added by a butterfly), each lane group computing RPT rows.  CAP_NZ / CAP_ROWS / XCAP: capacity of one
 // stage (entries, rows, staged x elements).  MINB CTAs of NT + 32 threads are
 // meant to share an SM.
-template <int NT_, int CAP_NZ_, int CAP_ROWS_, int XCAP_, int MINB_, int RPT_ = 1>
+template <int NT_, int CAP_NZ_, int CAP_ROWS_, int XCAP_, int MINB_, int RPT_ = 1, int E_ = 1>
 struct KCfg {
   static constexpr int NT = NT_, CAP_NZ = CAP_NZ_, CAP_ROWS = CAP_ROWS_, XCAP = XCAP_;
   static constexpr int MINB = MINB_, RPT = RPT_;
-  static constexpr int TILE_ROWS = NT * RPT;
+  static constexpr int E = E_;                       // lanes sharing one row (rows mode)
+  static constexpr int TILE_ROWS = NT * RPT / E;
+  static_assert(E == 1 || E == 2 || E == 4, "1, 2 or 4 lanes per row");
 };
 
 // Rows mode, short rows, FP64 values: 256 consumers (8 warps: two on each SM
@@ -129,13 +132,15 @@ struct KCfg {
 // registers), so each warp pays the shared-memory latency chain once per two
 // rows and the producer -- whose bulk copies cost a fixed ~170 cycles each to
 // issue -- starts half as many tiles per row.
-// Rows mode, long rows: 128 consumers, two CTAs per SM, stages of 3584
-// entries: rows of up to 28 entries.
+// Rows mode, long rows: 256 consumers, two lanes per row (each keeping up
+// to 14 of the row's entries in registers, so eight consumer warps fit the
+// registers of two CTAs per SM), tiles of 128 rows, stages of 3584 entries:
+// rows of up to 28 entries stay in registers.
 // Slices mode: 256 consumers, two CTAs per SM, balanced tiles of up to 2048
 // entries and 512 rows.
 using CfgShort = KCfg<256, 1792, 256, 1280, 3, 1>;
 using CfgShortNarrow = KCfg<256, 3584, 512, 2560, 3, 2>;
-using CfgLong = KCfg<128, 3584, 128, 1536, 2, 1>;
+using CfgLong = KCfg<256, 3584, 128, 1536, 2, 1, 2>;
 using CfgSlices = KCfg<256, 2048, 512, 1280, 2, 1>;
 
 constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -504,13 +509,17 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
     const I *is = reinterpret_cast<const I *>(st + L::OFF_I) + h1.z;
     const A *xs = reinterpret_cast<const A *>(st + L::OFF_X);
     const int r0 = h0.x, nr = h0.y, k0 = h0.z;
+    // lane ei of the E lanes of a row takes the row's entries ei, ei + E, ...
+    constexpr int E = C::E;
+    constexpr int UL = U / E;  // entries per lane kept in registers
+    const int ei = ctid % E;
     // the thread's RPT rows: operands of all of them into registers first
-    A av[C::RPT][U], xv[C::RPT][U];
+    A av[C::RPT][UL], xv[C::RPT][UL];
     int b[C::RPT], cnt[C::RPT];
     bool fits = true;
 #pragma unroll
     for (int rr = 0; rr < C::RPT; ++rr) {
-      const int lr = ctid + rr * C::NT;
+      const int lr = ctid / E + rr * (C::NT / E);
       b[rr] = 0;
       cnt[rr] = 0;
       if (lr < nr) {
@@ -518,11 +527,12 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
         cnt[rr] = rp[lr + 1] - k0 - b[rr];
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (u < cnt[rr]) {
-          const int cl = DA ? lr + static_cast<int>(is[b[rr] + u])
-                            : static_cast<int>(is[b[rr] + u]) - r0;
-          av[rr][u] = to_acc(vs[b[rr] + u]);
+      for (int u = 0; u < UL; ++u) {
+        const int q = ei + u * E;
+        if (q < cnt[rr]) {
+          const int cl = DA ? lr + static_cast<int>(is[b[rr] + q])
+                            : static_cast<int>(is[b[rr] + q]) - r0;
+          av[rr][u] = to_acc(vs[b[rr] + q]);
           xv[rr][u] = xs[xm.slot(cl)];
         }
       }
@@ -536,18 +546,19 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
     }
 #pragma unroll
     for (int rr = 0; rr < C::RPT; ++rr) {
-      const int lr = ctid + rr * C::NT;
-      if (lr < nr) {
-        A acc = 0;
+      const int lr = ctid / E + rr * (C::NT / E);
+      A acc = 0;
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (u < cnt[rr]) acc = fma_acc(av[rr][u], xv[rr][u], acc);
-        for (int q = b[rr] + U; q < b[rr] + cnt[rr]; ++q) {  // rows longer than U
-          const int cl = DA ? lr + static_cast<int>(is[q]) : static_cast<int>(is[q]) - r0;
-          acc = fma_acc(to_acc(vs[q]), xs[xm.slot(cl)], acc);
-        }
-        store_row<PLAIN>(p, r0 + lr, acc, dsum);
+      for (int u = 0; u < UL; ++u)
+        if (ei + u * E < cnt[rr]) acc = fma_acc(av[rr][u], xv[rr][u], acc);
+      for (int q = ei + UL * E; q < cnt[rr]; q += E) {  // rows longer than U
+        const int cl = DA ? lr + static_cast<int>(is[b[rr] + q])
+                          : static_cast<int>(is[b[rr] + q]) - r0;
+        acc = fma_acc(to_acc(vs[b[rr] + q]), xs[xm.slot(cl)], acc);
       }
+#pragma unroll
+      for (int o = 1; o < E; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lr < nr && ei == 0) store_row<PLAIN>(p, r0 + lr, acc, dsum);
     }
     if (!fits) {
       __syncwarp();

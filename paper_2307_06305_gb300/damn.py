@@ -128,10 +128,8 @@ _OPTIONAL = {}
 
 
 def _opt(name, res, args):
-    try:
-        _OPTIONAL[name] = _sig(name, res, args)
-    except AttributeError:
-        pass
+    """Declares a required symbol (a missing one fails the import)."""
+    _OPTIONAL[name] = _sig(name, res, args)
 
 
 _opt("damn_rcm_order", ctypes.c_int, [I32, I64, P, P, P, ctypes.POINTER(I64), ctypes.POINTER(I64)])

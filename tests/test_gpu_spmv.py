@@ -5,7 +5,7 @@
   product, 4 * nnz_row * 2^-53 * sum |a x| (alpha = 1, beta = 0) and its
   alpha/beta extension;
 * CSR-32 and DA-CSR-16 results bitwise equal under one plan;
-* every tiling mode (no plan, one row per thread with 224 / 128 consumers,
+* every tiling mode (no plan, one row per thread with 256 / 128 consumers,
   balanced slices), ragged sizes, empty rows, long rows (tiles computed from
   global memory), non-square shapes, beta = 0 with NaN in y;
 * reduced-precision values (FP32 / BF16, FP32 vectors and accumulation).
