@@ -87,9 +87,9 @@ k_csr_to_dacsr(int nrows, int ncols, const int *__restrict__ rowptr, const int *
        w * 32 < nrows; w += nwarps) {
     const int r0 = static_cast<int>(w * 32);
     const int nr = min(32, nrows - r0);
-    const int start = __ldg(rowptr + r0 + min(lane, nr));   // lane nr: end of the last row
+    const int start = __ldg(rowptr + r0 + min(lane, nr - 1));  // start of row r0 + lane
     const int k0 = __shfl_sync(0xffffffffu, start, 0);
-    const int k1 = __shfl_sync(0xffffffffu, start, nr);
+    const int k1 = __ldg(rowptr + r0 + nr);                      // end of the warp's rows
     for (int kb = k0; kb < k1; kb += 32) {
       const int k = kb + lane;
       // largest j < nr with start_j <= k (rows may be empty)
