@@ -1,9 +1,10 @@
 // CSR -> DA-CSR translation with the 16-bit (or 8-bit) fit check (Section 2,
 // Example 1, Eq. (2)), CSR validation, and round-to-nearest value casts.
 //
-// Each warp owns 32 consecutive rows and walks their entries with coalesced
-// loads of col and coalesced stores of off, finding each entry's row by a
-// binary search over the rows' starts held in the warp's registers.  Per-entry work is an int32 subtraction, a narrowing store
+// Each CTA owns a block of kRowsPerBlock rows: it stages their row pointers
+// in shared memory and walks the block's entries with coalesced loads of col
+// and coalesced stores of off, finding each entry's row by binary search in
+// shared memory.  Per-entry work is an int32 subtraction, a narrowing store
 // and min/max/count reductions; the kernel is bound by HBM traffic (4 bytes
 // read + 2 (or 1) bytes written per entry, plus 4 bytes per row).
 #include <algorithm>
@@ -70,46 +71,29 @@ __device__ __forceinline__ void block_reduce_fit(int mn, int mx, unsigned long l
 }
 
 // OffT = int16_t (DA-CSR-16) or int8_t (DA-CSR-8): an entry fits when its
-// offset lies in OffT's range.  Each warp takes 32 consecutive rows (lane l
-// holds the start of row r0 + l) and sweeps their entries with coalesced
-// loads and stores; an entry finds its row by a binary search over the 32
-// starts through shuffles.
+// offset lies in OffT's range.
 template <typename OffT>
 __global__ void __launch_bounds__(kConvThreads)
 k_csr_to_dacsr(int nrows, int ncols, const int *__restrict__ rowptr, const int *__restrict__ col,
                OffT *__restrict__ off, FitAccum *acc) {
   constexpr int kLo = -(1 << (8 * sizeof(OffT) - 1)), kHi = (1 << (8 * sizeof(OffT) - 1)) - 1;
-  const int lane = threadIdx.x & 31;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  __shared__ int rp[kRowsPerBlock + 1];
+  const int r0 = blockIdx.x * kRowsPerBlock;
+  const int nr = min(kRowsPerBlock, nrows - r0);
+  for (int i = threadIdx.x; i <= nr; i += kConvThreads) rp[i] = rowptr[r0 + i];
+  __syncthreads();
+  const int k0 = rp[0], k1 = rp[nr];
   int mn = INT_MAX, mx = INT_MIN;
   unsigned long long nf = 0, nb = 0;
-  for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-       w * 32 < nrows; w += nwarps) {
-    const int r0 = static_cast<int>(w * 32);
-    const int nr = min(32, nrows - r0);
-    const int start = __ldg(rowptr + r0 + min(lane, nr - 1));  // start of row r0 + lane
-    const int k0 = __shfl_sync(0xffffffffu, start, 0);
-    const int k1 = __ldg(rowptr + r0 + nr);                      // end of the warp's rows
-    for (int kb = k0; kb < k1; kb += 32) {
-      const int k = kb + lane;
-      // largest j < nr with start_j <= k (rows may be empty)
-      int j = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int cand = j + step;
-        const int sc = __shfl_sync(0xffffffffu, start, cand & 31);
-        if (cand < nr && sc <= k) j = cand;
-      }
-      if (k < k1) {
-        const int c = __ldcs(col + k);
-        const int d = c - (r0 + j);  // |d| < 2^31 since 0 <= r, c < 2^31
-        off[k] = static_cast<OffT>(d);
-        mn = min(mn, d);
-        mx = max(mx, d);
-        nf += (d >= kLo && d <= kHi) ? 1ull : 0ull;
-        nb += (c < 0 || c >= ncols) ? 1ull : 0ull;
-      }
-    }
+  for (int k = k0 + threadIdx.x; k < k1; k += kConvThreads) {
+    const int lr = row_of(rp, nr, k);
+    const int c = __ldcs(col + k);
+    const int d = c - (r0 + lr);  // |d| < 2^31 since 0 <= r, c < 2^31
+    off[k] = static_cast<OffT>(d);
+    mn = min(mn, d);
+    mx = max(mx, d);
+    nf += (d >= kLo && d <= kHi) ? 1ull : 0ull;
+    nb += (c < 0 || c >= ncols) ? 1ull : 0ull;
   }
   block_reduce_fit<kConvThreads>(mn, mx, nf, nb, acc);
 }
@@ -201,9 +185,7 @@ static int csr_to_dacsr(const char *fn, int32_t nrows, int32_t ncols, int64_t nn
   k_fit_init<<<1, 1, 0, s>>>(acc);
   DAMN_CHECK_LAUNCH("k_fit_init");
   if (nrows > 0) {
-    const long long warps = (nrows + 31LL) / 32;
-    const int blocks = (int)std::max<long long>(
-        1, std::min<long long>(8LL * sm_count(), (warps * 32 + kConvThreads - 1) / kConvThreads));
+    const int blocks = (nrows + kRowsPerBlock - 1) / kRowsPerBlock;
     k_csr_to_dacsr<OffT><<<blocks, kConvThreads, 0, s>>>(nrows, ncols, rowptr, col, off_out, acc);
     DAMN_CHECK_LAUNCH("k_csr_to_dacsr");
   }
