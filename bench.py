@@ -82,10 +82,16 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the SpMV kernel's sources with comments and blank lines
+    removed (a comment edit does not invalidate recorded counters)."""
+    import re
     h = hashlib.sha256()
     for name in ("spmv_kernel.cuh", "spmv.cu", "damn_common.cuh"):
-        with open(os.path.join(ROOT, "paper_2307_06305_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2307_06305_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        code = [re.sub(r"//.*$", "", line).rstrip() for line in text.splitlines()]
+        h.update("\n".join(l for l in code if l.strip()).encode())
     return h.hexdigest()[:16]
 
 

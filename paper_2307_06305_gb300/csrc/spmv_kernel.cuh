@@ -1,6 +1,7 @@
 // Device side of the SpMV engine: y <- alpha A x + beta y for CSR-32,
-// DA-CSR-16 and DA-CSR-8 (Section 4, Listing 2) with FP64 values, or FP32 / BF16 values
-// with FP32 vectors and FP32 accumulation.  Included by spmv.cu only.
+// DA-CSR-16 and DA-CSR-8 (Section 4, Listing 2) with FP64 values, or FP32 /
+// BF16 values with FP32 vectors and FP32 accumulation.  Included by spmv.cu
+// only.
 //
 // Design (GB300, sm_103a)
 // -----------------------
@@ -12,33 +13,41 @@
 //    the tile's x window -- the few contiguous x segments the tile's columns
 //    fall into, found at plan time -- into a ring of shared-memory stages with
 //    bulk asynchronous copies (cp.async.bulk, evict-first for the matrix)
-//    completing on an mbarrier;
+//    completing on an mbarrier.  Lane i of the producer prepares tile i
+//    (copy ranges, stage header) 32 tiles at a time; the serial per-tile work
+//    is the stage wait, the header stores, the byte count and the copies
+//    (each copy costs its issuing thread ~170 cycles on this part);
 //  * the consumers compute the tile entirely from shared memory: DA-CSR reads
 //    x at row + off (the shifted view of Listing 2), CSR at col, through a
-//    branch-free map from the column to its slot in the staged window.  Tiles
-//    whose window does not fit a stage gather x from global memory instead.
+//    branch-free map from the tile-local column to its slot in the staged
+//    window.  Tiles whose window does not fit a stage gather x from global
+//    memory instead.
 //
 // Staging x is what lets the FP64 FMAs overlap the matrix stream: on this part
-// a DFMA warp instruction occupies an SM sub-partition's FP64 unit for ~70
+// a DFMA warp instruction occupies an SM sub-partition's FP64 unit for ~67
 // cycles whatever the active lanes, so the FMA chains must never wait for
 // ~1 us L2 gathers.
 //
-// Two compute modes keep FP64 FMA lanes dense:
+// Compute modes (chosen per plan from the row-length statistics):
 //
-//  mode 0 (one row per thread): thread i owns row i of the tile and runs the
-//    row's FMA chain in stored order.  Each warp loads its rows (values and x
-//    into registers), hands the stage back, then runs the FMAs; the warps do
-//    not wait for each other.  For rows of nearly equal length.
-//  mode 1 (balanced slices): the tile's m entries are cut into NT contiguous
-//    slices of ceil(m/NT); every thread runs exactly its slice's FMAs,
-//    writing finished rows to shared memory and the partial sum of a row that
+//  rows (mode 0): E lanes per row (E = 1 for short rows, 2 for rows of a few
+//    dozen entries), each lane running its share of the row's FMA chain in
+//    stored order (E = 2: entries e, e + 2, ... per lane, then one shuffle
+//    add).  A warp loads its rows' values and x into registers, hands the
+//    stage back at once, then runs the FMAs; warps never wait for each other.
+//    FP64 short rows: 8 consumer warps per CTA and three CTAs per SM, six
+//    consumer warps per sub-partition to hide the shared-memory latency;
+//    FP32 / BF16 short rows: two rows per thread.
+//  slices (mode 1): the tile's m entries are cut into NT contiguous slices
+//    of ceil(m/NT); every thread runs exactly its slice's FMAs, writing
+//    finished rows to shared memory and the partial sum of a row that
 //    continues into the next slice to carry[i].  After a barrier, the thread
 //    that finishes a row begun in an earlier slice adds the carries of the
-//    slices the row spans, left to right.
+//    slices the row spans, left to right.  For irregular rows.
 //
-// Summation order depends only on the tile partition and NT, so for one plan
-// CSR-32 and DA-CSR-16 give bitwise equal results.  Tiles whose entries do not
-// fit a stage are computed in the plan's mode from global memory.
+// Summation order depends only on the plan (tile partition, mode, NT, E), so
+// for one plan CSR-32, DA-CSR-16 and DA-CSR-8 give bitwise equal results.
+// Tiles whose entries do not fit a stage are computed from global memory.
 //
 // Every mbarrier wait is bounded (global timer); a wait that gives up records
 // DAMN_ERR_TIMEOUT in the library status word, and the CTA drains its own
