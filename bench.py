@@ -65,6 +65,7 @@ METRIC = "DA-CSR16 vs CSR32 SpMV GB/s, % HBM peak; mixed-prec CG time-to-1e-10"
 WORKLOAD = "laplace3d_7pt_128^3_natural_dacsr16_f64_spmv"
 GRID = 128
 NCOPY = 4
+FP64_TFMA_NOMINAL = 0.625   # GB300 FP64: 1.25 TFLOP/s nominal, one FMA = 2 flops
 
 
 def spmv_bytes(n, nnz, idx_bytes, val_bytes, vec_bytes):
@@ -790,7 +791,12 @@ def main():
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
                      "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-                     "algorithmic_bytes_per_launch": b_da},
+                     "algorithmic_bytes_per_launch": b_da,
+                     # the second bound of FP64 SpMV on this part: one FMA per entry
+                     "fp64": {"achieved_tfma_per_s": round(nnz / per_step_da / 1e12, 4),
+                              "peak_tfma_per_s": FP64_TFMA_NOMINAL,
+                              "frac": round(nnz / per_step_da / 1e12 / FP64_TFMA_NOMINAL, 4),
+                              "peak_kind": "nominal 1.25 TFLOP/s FP64 = 0.625 TFMA/s"}},
         "csr32": {"gbs": round(b_cs / per_step_cs / 1e9, 1), "us": round(per_step_cs * 1e6, 2),
                   "speedup_da16_over_csr32": round(per_step_cs / per_step_da, 4),
                   "model_speedup": round(b_cs / b_da, 4)},
