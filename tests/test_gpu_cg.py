@@ -100,3 +100,17 @@ def test_cg_not_converged_and_zero_rhs(D, cuda_dev):
     res = D.damn_cg(S["t_rp"], S["t_off"], S["t_val"], S["t_b"], x, rtol=1e-8, max_iter=10)
     assert res["converged"] and res["iterations"] <= 1
     assert D.damn_device_status() == 0
+
+
+def test_cg_breakdown_reported_and_x_kept(D, cuda_dev):
+    """A negative definite matrix makes p.q < 0 at the first step: CG stops
+    with DAMN_ERR_NOT_CONVERGED (breakdown) without touching x and without
+    hanging."""
+    S = _system(cuda_dev, "lap2d", 16)
+    neg = -S["t_val"]
+    x0 = torch.full((S["n"],), 0.25, dtype=torch.float64, device=cuda_dev)
+    x = x0.clone()
+    res = D.damn_cg(S["t_rp"], S["t_off"], neg, S["t_b"], x, rtol=1e-10, max_iter=50)
+    assert res["status"] == D.DAMN_ERR_NOT_CONVERGED and not res["converged"]
+    assert torch.equal(x, x0)
+    assert D.damn_device_status(reset=True) == D.DAMN_OK
