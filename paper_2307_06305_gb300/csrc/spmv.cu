@@ -37,7 +37,7 @@ static_assert(CfgShort::TILE_ROWS <= CfgShort::CAP_ROWS &&
 // ----------------------------------------------------------------------------
 // Launch
 // ----------------------------------------------------------------------------
-template <bool PLAIN, typename V, typename I, class C>
+template <bool PLAIN, typename V, typename I, class C, int NS>
 int launch_kernel(SpmvParams p, cudaStream_t s, int *gs_out) {
   using L = Layout<V, I, C>;
   // per device and mode: chosen ring depth and CTAs per SM (0 = not yet known)
@@ -52,14 +52,14 @@ int launch_kernel(SpmvParams p, cudaStream_t s, int *gs_out) {
     if (!occ_of[dev][mode]) {
       int max_optin = 0;
       DAMN_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-      DAMN_CUDA(cudaFuncSetAttribute(k_spmv<PLAIN, V, I, C>,
+      DAMN_CUDA(cudaFuncSetAttribute(k_spmv<PLAIN, V, I, C, NS>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin));
       // deepest ring that keeps C::MINB CTAs per SM (at least two stages)
       int best_s = 2, best_o = 0;
       for (int st = kMaxStages; st >= 2; --st) {
         if (L::total(st, mode) > (size_t)max_optin) continue;
         int o = 0;
-        DAMN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_spmv<PLAIN, V, I, C>,
+        DAMN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_spmv<PLAIN, V, I, C, NS>,
                                                                 C::NT + 32, L::total(st, mode)));
         if (o >= C::MINB) { best_s = st; best_o = o; break; }
         if (o > best_o) { best_s = st; best_o = o; }
@@ -72,7 +72,7 @@ int launch_kernel(SpmvParams p, cudaStream_t s, int *gs_out) {
   const int grid = std::max(1, std::min(p.ntiles, occ_of[dev][mode] * sm_count()));
   if (gs_out) { gs_out[0] = grid; gs_out[1] = p.stages; }
   if (p.ntiles == 0) return DAMN_OK;
-  k_spmv<PLAIN, V, I, C><<<grid, C::NT + 32, L::total(p.stages, mode), s>>>(p);
+  k_spmv<PLAIN, V, I, C, NS><<<grid, C::NT + 32, L::total(p.stages, mode), s>>>(p);
   DAMN_CHECK_LAUNCH("k_spmv");
   return DAMN_OK;
 }
@@ -80,8 +80,14 @@ int launch_kernel(SpmvParams p, cudaStream_t s, int *gs_out) {
 template <typename V, typename I, class C>
 int launch_cfg(const SpmvParams &p, cudaStream_t s, int *gs) {
   const bool plain = p.ab_mode == 0 && !p.dot_w && !p.dot_self && !p.dot_partials;
-  if (plain) return launch_kernel<true, V, I, C>(p, s, gs);
-  return launch_kernel<false, V, I, C>(p, s, gs);
+  // rows mode with every x window of at most 3 segments: one compare fewer
+  // per entry in the column -> slot map
+  if (p.mode == 0 && p.max_nseg <= 3) {
+    if (plain) return launch_kernel<true, V, I, C, 3>(p, s, gs);
+    return launch_kernel<false, V, I, C, 3>(p, s, gs);
+  }
+  if (plain) return launch_kernel<true, V, I, C, kXSegMax>(p, s, gs);
+  return launch_kernel<false, V, I, C, kXSegMax>(p, s, gs);
 }
 
 template <typename V, typename I>
@@ -295,12 +301,21 @@ k_plan_xseg(int nrows, int ncols, const int *__restrict__ rowptr, const void *id
   }
 }
 
+// count[0]: tiles with a staged x window; count[1]: most segments of a window
 __global__ void k_count_staged(const XSeg *xs, int ntiles, int *count) {
-  int c = 0;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
+  int c = 0, mx = 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
     c += xs[t].nseg > 0 ? 1 : 0;
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+    mx = max(mx, xs[t].nseg);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (c) atomicAdd(count, c);
+    atomicMax(count + 1, mx);
+  }
 }
 
 }  // namespace
@@ -323,6 +338,7 @@ struct damn_plan {
   XSeg *d_xseg;           // x windows of the current tiling (NULL: none)
   int xseg_cap;
   int staged_tiles;
+  int max_nseg;           // most x segments of a tile's window (rows mode kernel variant)
   int max_row;
   double row_eff;
   int max_tile_short, max_tile_long;
@@ -372,6 +388,7 @@ static int make_params(const SpmvCall &c, const damn_plan *plan, SpmvParams &p, 
     p.ntiles = plan->ntiles;
     p.bounds = plan->d_bounds;
     p.xseg = plan->d_xseg;
+    p.max_nseg = plan->d_xseg ? plan->max_nseg : kXSegMax;
     shape = plan->shape;
   } else {
     p.mode = 1;
@@ -379,6 +396,7 @@ static int make_params(const SpmvCall &c, const damn_plan *plan, SpmvParams &p, 
     p.ntiles = (c.nrows + 255) / 256;
     p.bounds = nullptr;
     p.xseg = nullptr;
+    p.max_nseg = kXSegMax;
     shape = 2;
   }
   return DAMN_OK;
@@ -472,6 +490,7 @@ static void plan_free_device(damn_plan *pl) {
 // Recomputes the x windows for the plan's current tiling (synchronises).
 static int plan_xwindows(damn_plan *pl, cudaStream_t s) {
   pl->staged_tiles = 0;
+  pl->max_nseg = kXSegMax;
   if (!pl->idx || pl->ntiles == 0 || pl->nrows == 0) return DAMN_OK;
   if (pl->xseg_cap < pl->ntiles) {
     if (pl->d_xseg) cudaFree(pl->d_xseg);
@@ -490,15 +509,16 @@ static int plan_xwindows(damn_plan *pl, cudaStream_t s) {
                                      16 / asz, pl->d_xseg);
   DAMN_CHECK_LAUNCH("k_plan_xseg");
   int *d_cnt = nullptr;
-  DAMN_CUDA(cudaMallocAsync(&d_cnt, sizeof(int), s));
-  DAMN_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int), s));
+  DAMN_CUDA(cudaMallocAsync(&d_cnt, 2 * sizeof(int), s));
+  DAMN_CUDA(cudaMemsetAsync(d_cnt, 0, 2 * sizeof(int), s));
   k_count_staged<<<std::min(1024, (pl->ntiles + 255) / 256), 256, 0, s>>>(pl->d_xseg, pl->ntiles,
                                                                           d_cnt);
-  int h = 0;
-  DAMN_CUDA(cudaMemcpyAsync(&h, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int h[2] = {0, 0};
+  DAMN_CUDA(cudaMemcpyAsync(h, d_cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   DAMN_CUDA(cudaFreeAsync(d_cnt, s));
   DAMN_CUDA(cudaStreamSynchronize(s));
-  pl->staged_tiles = h;
+  pl->staged_tiles = h[0];
+  pl->max_nseg = h[1];
   return DAMN_OK;
 }
 

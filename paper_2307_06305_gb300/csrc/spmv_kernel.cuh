@@ -112,6 +112,7 @@ struct SpmvParams {
   int dot_self;
   double *dot_partials;
   int stages;          // depth of the shared-memory ring (<= kMaxStages)
+  int max_nseg;        // most x segments of any tile's window
   int *status;
   unsigned long long timeout_ns;
 };
@@ -402,6 +403,15 @@ struct XMap {
   __device__ __forceinline__ int slot(int cl) const {
     return cl + d0 + (cl >= lo1 ? dd1 : 0) + (cl >= lo2 ? dd2 : 0) + (cl >= lo3 ? dd3 : 0);
   }
+  // the same when the window has at most NS segments
+  template <int NS>
+  __device__ __forceinline__ int slot_n(int cl) const {
+    int r = cl + d0;
+    if (NS > 1) r += cl >= lo1 ? dd1 : 0;
+    if (NS > 2) r += cl >= lo2 ? dd2 : 0;
+    if (NS > 3) r += cl >= lo3 ? dd3 : 0;
+    return r;
+  }
 };
 
 // y[row] <- alpha acc + beta y0[row] (+ optional fused dot).  PLAIN is the
@@ -488,7 +498,7 @@ __device__ __noinline__ void rows_general(const SpmvParams &p, unsigned char *sm
 // loads its rows' values and x into registers, hands the stage back, then
 // runs the FMA chains, so the warps of a CTA do not wait for each other.
 // Rows longer than U entries finish from the stage before it is released.
-template <bool PLAIN, typename V, typename I, class C>
+template <bool PLAIN, typename V, typename I, class C, int NS>
 __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char *smem,
                                              uint64_t *full, uint64_t *empty, const TileHdr *hdr,
                                              int ctid, double &dsum) {
@@ -542,7 +552,7 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
           const int cl = DA ? lr + static_cast<int>(is[b[rr] + q])
                             : static_cast<int>(is[b[rr] + q]) - r0;
           av[rr][u] = to_acc(vs[b[rr] + q]);
-          xv[rr][u] = xs[xm.slot(cl)];
+          xv[rr][u] = xs[xm.template slot_n<NS>(cl)];
         }
       }
       fits = fits && cnt[rr] <= U;
@@ -563,7 +573,7 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
       for (int q = ei + UL * E; q < cnt[rr]; q += E) {  // rows longer than U
         const int cl = DA ? lr + static_cast<int>(is[b[rr] + q])
                           : static_cast<int>(is[b[rr] + q]) - r0;
-        acc = fma_acc(to_acc(vs[b[rr] + q]), xs[xm.slot(cl)], acc);
+        acc = fma_acc(to_acc(vs[b[rr] + q]), xs[xm.template slot_n<NS>(cl)], acc);
       }
 #pragma unroll
       for (int o = 1; o < E; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -658,7 +668,7 @@ __device__ __forceinline__ void tile_slices(const SpmvParams &p, const TileHdr &
 // ----------------------------------------------------------------------------
 // Kernel
 // ----------------------------------------------------------------------------
-template <bool PLAIN, typename V, typename I, class C>
+template <bool PLAIN, typename V, typename I, class C, int NS>
 __global__ void __launch_bounds__(C::NT + 32, C::MINB) k_spmv(const SpmvParams p) {
   using A = typename AccOf<V>::type;
   using L = Layout<V, I, C>;
@@ -686,7 +696,7 @@ __global__ void __launch_bounds__(C::NT + 32, C::MINB) k_spmv(const SpmvParams p
   const int ctid = tid - 32;
   double dsum = 0.0;
   if (p.mode == 0) {
-    consume_rows<PLAIN, V, I, C>(p, smem, full, empty, hdr, ctid, dsum);
+    consume_rows<PLAIN, V, I, C, NS>(p, smem, full, empty, hdr, ctid, dsum);
   } else {
     int j = 0;
     for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++j) {
