@@ -307,7 +307,7 @@ int damn_spmv_dabsr8(int32_t nbr, int32_t nbc, int64_t nblk, int32_t b, const in
 /* DA-COO: diagonal addressing of the column vector of COO storage           */
 /* (Section 1)                                                               */
 /* ------------------------------------------------------------------------ */
-/* Workspace bytes for the COO SpMVs below (two partial sums per chunk of 8
+/* Workspace bytes for the COO SpMVs below (two partial sums per tile of 2048
  * entries). */
 size_t damn_coo_workspace_size(int64_t nnz, int dtype);
 
@@ -315,11 +315,14 @@ size_t damn_coo_workspace_size(int64_t nnz, int dtype);
  * entry its column (coo32: col int32) or its offset from the diagonal
  * (dacoo16: c - r as int16, e.g. from damn_csr_to_dacsr on the same entries),
  * values val[nnz] of dtype (as for damn_spmv_dacsr16).  Entries of a row in
- * stored order are summed with FMA in chunks of 8 consecutive entries; a row
- * crossing chunks adds its chunk sums left to right.  Deterministic (no
- * atomics); coo32 and dacoo16 give bitwise equal results.  Rows without
- * entries get beta y (0 when beta == 0).  workspace: device, 16-byte aligned,
- * >= damn_coo_workspace_size(nnz, dtype) bytes.  Asynchronous. */
+ * stored order are summed with FMA in chunks of 8 consecutive entries (chunk
+ * j = entries 8j .. 8j+7); a row crossing chunks adds its chunk sums left to
+ * right.  y[r] = alpha * sum + beta * y[r], y not read when beta == 0.
+ * Deterministic (no atomics); coo32 and dacoo16 give bitwise equal results.
+ * Rows without entries get beta y (0 when beta == 0).  Row indices outside
+ * [0, nrows) are never written.  16-byte aligned row, idx and val arrays are
+ * read with 16-byte loads.  workspace: device, 16-byte aligned,
+ * >= damn_coo_workspace_size(nnz, dtype) bytes.  Two launches, asynchronous. */
 int damn_spmv_coo32(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *row,
                     const int32_t *col, const void *val, int dtype, const void *x, void *y,
                     double alpha, double beta, void *workspace, size_t ws_bytes, void *stream);

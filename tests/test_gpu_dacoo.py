@@ -91,3 +91,44 @@ def test_dacoo_alpha_beta_and_empty(D, cuda_dev):
     e = np.zeros(0, dtype=np.int32)
     y = _run(D, cuda_dev, n, rp0, e, np.zeros(0), x, beta=2.0, y0=y0)
     assert np.array_equal(y, 2.0 * y0)
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_dacoo_tiles_long_rows_gaps_unaligned(D, cuda_dev, dt):
+    """Rows longer than a tile of 2048 entries (finished across tiles), a run
+    of 3000 empty rows (owned rows beyond one shared-memory window), and
+    arrays that are not 16-byte aligned (element loads instead of 16-byte
+    loads): dyadic inputs make every summation order exact, so the result
+    equals the oracle bitwise on both load paths."""
+    rng = np.random.default_rng(5)
+    n = 40000
+    lens = rng.integers(0, 12, size=n)
+    lens[10000:13000] = 0
+    lens[20000], lens[20001], lens[30000] = 5000, 2048, 4097
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    rp = rp.astype(np.int32)
+    r = np.repeat(np.arange(n), lens)
+    col = np.clip(r + rng.integers(-2000, 2001, size=len(r)), 0, n - 1).astype(np.int32)
+    val = rng.integers(-4, 5, size=len(col)).astype(np.float64)
+    x = W.dyadic_vector(n, rng, bits=8)
+    ref = OS.spmv(n, rp, col, val, x, diagonal_addressed=False)
+    row = OD.entry_rows(n, rp).astype(np.int32)
+    off = OD.translate(n, rp, col).astype(np.int16)
+    tx = _t(cuda_dev, x).to(dt)
+    outs = []
+    for shift in (0, 1):
+        def put(a, tdt=None):
+            t = torch.zeros(len(a) + shift, dtype=tdt or torch.from_numpy(a[:1]).dtype, device=cuda_dev)
+            t[shift:] = _t(cuda_dev, a).to(t.dtype)
+            return t[shift:]
+        tr, tc, to, tv = put(row), put(col), put(off), put(val, dt)
+        if shift:
+            assert tr.data_ptr() % 16 and to.data_ptr() % 16 and tv.data_ptr() % 16
+        for fn, idx in ((D.damn_spmv_coo32, tc), (D.damn_spmv_dacoo16, to)):
+            y = torch.full((n,), float("nan"), dtype=dt, device=cuda_dev)
+            fn(n, tr, idx, tv, tx, y)
+            outs.append(y.double().cpu().numpy())
+    torch.cuda.synchronize()
+    for y in outs:
+        assert np.array_equal(y, ref)
