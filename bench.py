@@ -35,6 +35,9 @@ none of them inside the headline's timed region):
   * ``dabsr``: DA-BSR-16 vs BSR-32 (diagonal addressing of the block
     pattern) on a 96^3 grid with dense 3 x 3 blocks, FP64 and FP32 values;
   * ``dacoo``: DA-COO-16 vs COO-32 on the 128^3 Laplacian;
+  * ``banded``: random banded matrices, n in {1e5, 1e6} x h in {100, 1000,
+    30000} and n = 1e7 at h = 1000, DA-CSR-16 vs CSR-32 FP64 (``banded_full``:
+    n in {1e5, 3e5, 1e6, 3e6, 1e7, 2e7} x the three h, not run by default);
   * ``small``: the 64x64 5-point Laplacian, SpMV time per call under graph
     replay (launch / latency bound, in L2).
 
@@ -550,6 +553,76 @@ def section_dacoo(D, torch, dev, reps):
     return out
 
 
+BANDED_POINTS = ((100_000, 100), (100_000, 1000), (100_000, 30000),
+                 (1_000_000, 100), (1_000_000, 1000), (1_000_000, 30000),
+                 (10_000_000, 1000))
+BANDED_POINTS_FULL = tuple((n, h) for n in (100_000, 300_000, 1_000_000, 3_000_000, 10_000_000,
+                                            20_000_000) for h in (100, 1000, 30000))
+L2_BYTES = 126e6
+TILING_NAMES = ("slices", "rows", "rows_long")   # DAMN_TILING_* 0, 1, 2
+
+
+def section_banded(D, torch, dev, reps, full=False):
+    """Random banded matrices (row lengths LogNormal(ln 12, 0.5), columns
+    uniform in [r - h, r + h]), DA-CSR-16 vs CSR-32 FP64 under each of the
+    three tilings; the best of each format is reported.  Small matrices are
+    replicated and cycled so that every step reads its matrix from HBM; x
+    (counted once) may stay in L2."""
+    import workloads as W
+    peak = measured_peaks()[0]["hbm_gbs"]
+    pts = BANDED_POINTS_FULL if full else BANDED_POINTS
+    out = {"workload": "random_banded_sweep", "points": []}
+    for i, (n, h) in enumerate(pts):
+        rp, col, val = W.random_banded(n, h, W.rng_for(3, i))
+        nnz = len(col)
+        b16, b32 = spmv_bytes(n, nnz, 2, 8, 8), spmv_bytes(n, nnz, 4, 8, 8)
+        copies = int(min(16, max(1, -(-3 * L2_BYTES // b16))))
+        t_rp = torch.from_numpy(rp).to(dev)
+        t_col = torch.from_numpy(col).to(dev)
+        t_val = torch.from_numpy(val).to(dev)
+        del rp, col, val
+        off, fi = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
+        mats = [(t_rp, t_col, off, t_val)] + [tuple(t.clone() for t in (t_rp, t_col, off, t_val))
+                                             for _ in range(copies - 1)]
+        plans = [D.Plan(m[0], nnz, n, torch.float64, idx=m[2]) for m in mats]
+        x = torch.from_numpy(W.uniform_vector(n, W.rng_for(3, 100 + i))).to(dev)
+        y = torch.empty(n, dtype=torch.float64, device=dev)
+        desc = plans[0].describe()
+        pt = {"n": n, "h": h, "nnz": nnz, "w": int(fi.w), "copies": copies,
+              "heuristic_tiling": TILING_NAMES[desc["tiling"]],
+              "row_efficiency": round(desc["row_efficiency"], 3), "max_row": desc["max_row"],
+              "tilings": {}}
+        for tiling, tname in enumerate(TILING_NAMES):
+            for pl in plans:
+                pl.set_tiling(tiling)
+            tt = {"x_staged_tiles_frac": round(plans[0].describe()["x_staged_tiles"]
+                                               / max(1, plans[0].describe()["ntiles"]), 3)}
+            for fmt, fn, k in (("da16", D.damn_spmv_dacsr16, 2), ("csr32", D.damn_spmv_csr32, 1)):
+                def step(j):
+                    m = mats[j % copies]
+                    fn(m[0], m[k], m[3], x, y, plan=plans[j % copies])
+                for j in range(3):
+                    step(j)
+                calls = 10 * copies
+                t, _ = _event_time(torch, lambda: [step(j) for j in range(calls)], max(3, reps // 2))
+                tt[fmt + "_us"] = round(t / calls * 1e6, 2)
+            pt["tilings"][tname] = tt
+        best = min(pt["tilings"], key=lambda k: pt["tilings"][k]["da16_us"])
+        bc = min(pt["tilings"], key=lambda k: pt["tilings"][k]["csr32_us"])
+        pt["best_tiling"] = best
+        pt["da16_us"] = pt["tilings"][best]["da16_us"]
+        pt["csr32_us"] = pt["tilings"][bc]["csr32_us"]
+        pt["da16_gbs"] = round(b16 / pt["da16_us"] / 1e3, 1)
+        pt["csr32_gbs"] = round(b32 / pt["csr32_us"] / 1e3, 1)
+        pt["da16_frac_hbm"] = round(pt["da16_gbs"] / peak, 3)
+        pt["speedup_da16_over_csr32"] = round(pt["csr32_us"] / pt["da16_us"], 4)
+        pt["model_speedup"] = round(b32 / b16, 4)
+        out["points"].append(pt)
+        del mats, plans, x, y, t_rp, t_col, t_val, off
+        torch.cuda.empty_cache()
+    return out
+
+
 def section_small(D, torch, dev, reps):
     """Config 1 size (64x64 5-point Laplacian, in L2): time per SpMV under
     graph replay of 1000 calls."""
@@ -587,7 +660,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--sections",
-                    default="conversion,solvers,solvers_perturbed,batched,da8,dabsr,dacoo,small",
+                    default="conversion,solvers,solvers_perturbed,batched,da8,dabsr,dacoo,banded,"
+                            "small",
                     help="comma list of secondary sections to run after the headline ('' for none)")
     ap.add_argument("--section-reps", type=int, default=10)
     ap.add_argument("--e2e-parts", type=int, default=1,
@@ -813,7 +887,8 @@ def main():
     fns = {"conversion": section_conversion_rcm, "solvers": section_solvers,
            "solvers_perturbed": lambda *a: section_solvers(*a, perturb=True),
            "batched": section_batched, "da8": section_da8, "dabsr": section_dabsr,
-           "dacoo": section_dacoo,
+           "dacoo": section_dacoo, "banded": section_banded,
+           "banded_full": lambda *a: section_banded(*a, full=True),
            "small": section_small}
     for name in secs:
         t0 = time.perf_counter()

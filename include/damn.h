@@ -226,7 +226,9 @@ typedef struct {
 
 /* Builds a plan for one matrix and value dtype: the partition of the rows
  * into tiles, the compute mode (chosen from the row-length statistics:
- * DAMN_TILING_ROWS or _ROWS_LONG when rows are uniform inside 32-row groups,
+ * DAMN_TILING_ROWS or _ROWS_LONG when rows are uniform inside 32-row groups;
+ * _ROWS_LONG also for ragged rows (row_efficiency >= 0.3) when its tiles fit
+ * a stage and at least 90 % of their x windows are staged;
  * DAMN_TILING_SLICES otherwise) and, when idx (col for DAMN_FMT_CSR32, off
  * for DAMN_FMT_DACSR16 / DAMN_FMT_DACSR8) is given, the x window of every
  * tile: the tile's sorted distinct columns cut into at most 4 contiguous

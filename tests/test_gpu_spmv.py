@@ -244,3 +244,26 @@ def test_bounded_wait_selftest(D, cuda_dev):
 
 def test_device_status_clean(D, cuda_dev):
     assert D.damn_device_status() == 0
+
+
+@pytest.mark.parametrize("h,expect", [(100, "rows_long"), (5000, "slices")])
+def test_heuristic_ragged_rows(D, cuda_dev, h, expect):
+    """Random banded rows (lengths LogNormal around 12, row efficiency about
+    0.4): the plan runs them two lanes per row when the 128-row tiles' x
+    windows are staged (narrow band), as balanced slices when they are not
+    (wide band); either way within the bound and CSR-32 == DA-CSR-16."""
+    rng = np.random.default_rng(21)
+    n = 20000
+    rp, col, val = W.random_banded(n, h, rng)
+    m = Mat(D, cuda_dev, n, n, rp, col, val)
+    plan = D.Plan(m.t_rp, len(m.col), n, torch.float64, idx=m.t_off)
+    d = plan.describe()
+    assert 0.3 <= d["row_efficiency"] < 0.85
+    want = {"rows_long": D.DAMN_TILING_ROWS_LONG, "slices": D.DAMN_TILING_SLICES}[expect]
+    assert d["tiling"] == want, d
+    if expect == "rows_long":
+        assert d["x_staged_tiles"] >= 0.9 * d["ntiles"]
+    x = W.uniform_vector(n, rng)
+    got = _run(D, m, x, plan=plan)
+    _bound_check(m, x, got)
+    assert np.array_equal(got, _run(D, m, x, plan=plan, fmt="csr"))
