@@ -206,7 +206,7 @@ int damn_rcm_permute(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_
 typedef struct damn_plan damn_plan;
 
 typedef struct {
-  int32_t mode;          /* 0 = one row per thread, 1 = balanced entry slices */
+  int32_t mode;          /* 0 = row tiles (ROWS, ROWS_LONG), 1 = balanced entry slices */
   int32_t tile_items;    /* rows per tile, or rows+entries budget of a balanced tile */
   int32_t ntiles;
   int32_t grid;          /* persistent CTAs of the last launch                 */
@@ -252,8 +252,8 @@ int damn_plan_autotune(damn_plan *plan, int format, const void *idx, const void 
  * entries, each computed as balanced entry slices), DAMN_TILING_ROWS (tiles
  * of 256 rows with FP64 values, one row per thread, or 512 rows with FP32 /
  * BF16 values, two rows per thread; short rows), DAMN_TILING_ROWS_LONG
- * (128-row tiles with larger stages, one row per thread; rows of a few
- * dozen).
+ * (128-row tiles with larger stages, two lanes per row whose partial sums
+ * are added at the end; rows of a few dozen).
  * Recomputes the x windows; synchronises the legacy default stream. */
 int damn_plan_set_tiling(damn_plan *plan, int tiling);
 
