@@ -872,9 +872,12 @@ def main():
                               "frac": round(nnz / per_step_da / 1e12 / FP64_TFMA_NOMINAL, 4),
                               "peak_kind": "nominal 1.25 TFLOP/s FP64 = 0.625 TFMA/s"}},
         "csr32": {"gbs": round(b_cs / per_step_cs / 1e9, 1), "us": round(per_step_cs * 1e6, 2),
+                  "gflops": round((2 * nnz + 2 * n) / per_step_cs / 1e9, 2),
                   "speedup_da16_over_csr32": round(per_step_cs / per_step_da, 4),
                   "model_speedup": round(b_cs / b_da, 4)},
         "da16_us": round(per_step_da * 1e6, 2),
+        # Section 4's work W = 2 nnz + 2 n per SpMV, over the same step time
+        "gflops": round((2 * nnz + 2 * n) / per_step_da / 1e9, 2),
         "mixed_precision_spmv": mixed,
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n, "us_per_step": round(t_e2e * 1e6, 2),
