@@ -649,6 +649,9 @@ def section_small(D, torch, dev, reps):
         g.replay()
         t, _ = _event_time(torch, g.replay, reps)
         out[f"{name}_us_per_spmv"] = round(t / 1000 * 1e6, 3)
+        # algorithmic bytes per SpMV over its time (the matrix stays in L2)
+        b = spmv_bytes(n, nnz, 2 if name == "da16" else 4, 8, 8)
+        out[f"{name}_gbs"] = round(b / (t / 1000) / 1e9, 1)
     return out
 
 
