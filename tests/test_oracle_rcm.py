@@ -149,3 +149,102 @@ def test_scrambled_laplacian_restored():
     p2 = reverse_cuthill_mckee(A, symmetric_mode=True)
     w2 = _perm_bandwidth(n, rp, c, p2)
     assert w <= 1.5 * w2 + 2
+
+
+def _selfloop_case():
+    """Path 0-1-2-3 with a self loop on vertex 0 only, worked by hand.  Self
+    loops are not edges: degrees 1, 2, 2, 1; the minimum (degree, index) is
+    0; L(0) = [0][1][2][3] and the last level's vertex 3 has no larger
+    eccentricity, so CM runs 0, 1, 2, 3 and the reversal gives 3, 2, 1, 0.
+    Counting the loop would give vertex 0 degree 2, start at 3 and return
+    0, 1, 2, 3."""
+    rp, c, _ = W.from_coo(4, [0, 0, 1, 1, 2, 2, 3], [0, 1, 0, 2, 1, 3, 2])
+    return "selfloop", 4, rp, c, [3, 2, 1, 0]
+
+
+def _pinned_cases():
+    out = []
+    for name, n, edges, perm in _hand_examples():
+        rp, c, _ = _graph_csr(n, edges)
+        out.append((name, n, rp, c, perm))
+    out.append(_selfloop_case())
+    return out
+
+
+def test_selfloop_hand_example():
+    name, n, rp, c, perm = _selfloop_case()
+    assert R.rcm_order(n, rp, c).tolist() == perm
+
+
+def _cm_sorted_by(key):
+    def cm(start, ptr, adj, deg, visited):
+        order = [start]
+        visited[start] = True
+        queue = [start]
+        while queue:
+            v = queue.pop(0)
+            nbrs = [u for u in adj[ptr[v]:ptr[v + 1]].tolist() if not visited[u]]
+            nbrs.sort(key=lambda t: key(int(deg[t]), t))
+            for u in nbrs:
+                visited[u] = True
+                order.append(u)
+                queue.append(u)
+        return order
+    return cm
+
+
+def _george_liu(pick, moves_on_equal=False):
+    def pp(start, ptr, adj, deg):
+        v = start
+        levels = R.level_structure(v, ptr, adj)
+        for _ in range(4 * len(ptr)):
+            u = pick(levels[-1], deg)
+            lu = R.level_structure(u, ptr, adj)
+            if len(lu) > len(levels) or (moves_on_equal and len(lu) == len(levels) and u != v):
+                v, levels = u, lu
+            else:
+                break
+        return v
+    return pp
+
+
+def _graph_with_loops_in_degree(n, rowptr, col):
+    ptr, adj, deg = ORIG_SYMMETRIC_GRAPH(n, rowptr, col)
+    r = D.entry_rows(n, rowptr)
+    has_loop = np.zeros(n, dtype=np.int64)
+    has_loop[r[r == np.asarray(col)]] = 1
+    return ptr, adj, deg + has_loop
+
+
+ORIG_SYMMETRIC_GRAPH = R.symmetric_graph
+
+
+@pytest.mark.parametrize("mistake", ["not_reversed", "ties_index_descending", "degree_descending",
+                                     "neighbours_by_index", "no_george_liu",
+                                     "george_liu_moves_on_equal", "last_level_by_index",
+                                     "self_loops_in_degree"])
+def test_planted_mistakes_are_caught(mistake, monkeypatch):
+    """Each plausible slip in the ordering changes at least one hand-worked
+    permutation (the mistake is planted in the oracle, on the CPU)."""
+    order = R.rcm_order
+    if mistake == "not_reversed":
+        order = lambda n, rp, c: R.rcm_order(n, rp, c)[::-1]
+    elif mistake == "ties_index_descending":
+        monkeypatch.setattr(R, "cuthill_mckee_from", _cm_sorted_by(lambda d, t: (d, -t)))
+    elif mistake == "degree_descending":
+        monkeypatch.setattr(R, "cuthill_mckee_from", _cm_sorted_by(lambda d, t: (-d, t)))
+    elif mistake == "neighbours_by_index":
+        monkeypatch.setattr(R, "cuthill_mckee_from", _cm_sorted_by(lambda d, t: t))
+    elif mistake == "no_george_liu":
+        monkeypatch.setattr(R, "pseudo_peripheral", lambda start, ptr, adj, deg: start)
+    elif mistake == "george_liu_moves_on_equal":
+        monkeypatch.setattr(R, "pseudo_peripheral",
+                            _george_liu(lambda last, deg: min(last, key=lambda t: (int(deg[t]), t)),
+                                        moves_on_equal=True))
+    elif mistake == "last_level_by_index":
+        monkeypatch.setattr(R, "pseudo_peripheral", _george_liu(lambda last, deg: min(last)))
+    else:
+        monkeypatch.setattr(R, "symmetric_graph", _graph_with_loops_in_degree)
+    wrong = [name for name, n, rp, c, perm in _pinned_cases()
+             if np.asarray(order(n, rp, c)).tolist() != perm]
+    assert wrong, mistake
