@@ -121,3 +121,35 @@ def test_int8_fit_of_grids():
         rp, c, _ = W.laplace2d_5pt(m)
         assert D.fit_check(m * m, m * m, rp, c, bits=8).fits == fits
         assert D.fit_check(m * m, m * m, rp, c, bits=16).fits
+
+
+@pytest.mark.parametrize("mistake", ["sign", "row_shift", "w_without_abs", "symmetric_fit",
+                                     "strict_upper"])
+def test_planted_mistakes_are_caught(mistake, monkeypatch, golden):
+    """Each plausible slip in the translation or the fit rule fails one of the
+    pins above (the mistake is planted in the oracle, on the CPU)."""
+    if mistake == "sign":
+        monkeypatch.setattr(D, "translate", lambda n, rp, c: D.entry_rows(n, rp) - np.asarray(c))
+    elif mistake == "row_shift":
+        real = D.entry_rows
+        monkeypatch.setattr(D, "entry_rows", lambda n, rp: np.minimum(real(n, rp) + 1, n - 1))
+    elif mistake == "w_without_abs":
+        monkeypatch.setattr(D, "bandwidth", lambda n, rp, c: int(np.max(D.translate(n, rp, c)))
+                            if len(c) else 0)
+    elif mistake == "symmetric_fit":
+        monkeypatch.setattr(D, "INT16_MIN", -32767)
+    else:
+        monkeypatch.setattr(D, "INT16_MAX", 32766)
+    pins = [lambda: test_example1(golden),
+            lambda: [test_bandwidth_brute_force(s) for s in range(5)],
+            test_explicit_zeros_count,
+            lambda: [test_int16_boundary(e, f) for e, f in
+                     ((32767, True), (-32767, True), (-32768, True), (32768, False),
+                      (-32769, False))]]
+    failed = 0
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            failed += 1
+    assert failed >= 1, mistake
