@@ -218,6 +218,55 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+PROFILE_CASES = ("stencil27_160_rows_long", "batch512_f64_k1")
+
+
+def run_case(args):
+    """--case NAME: only the launches of one kernel, for an ncu capture; no
+    timing (a number taken under a profiler is not a benchmark value).
+
+    stencil27_160_rows_long: the 160^3 27-point stencil converted to
+    DA-CSR-16, a plan pinned to the rows-long tiling, then --steps FP64 SpMVs
+    (every k_spmv launch of the run).
+    batch512_f64_k1: the 512 random banded matrices converted to DA-CSR-16,
+    k = 1 FP64 right-hand sides, a batch plan without autotuning, then
+    --steps direct launches of the batched kernel."""
+    import torch
+    import workloads as W
+    from paper_2307_06305_gb300 import damn as D
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    if args.case == "stencil27_160_rows_long":
+        rp, col, val = W.stencil27(160)
+        n, nnz = len(rp) - 1, len(col)
+        t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
+        off, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
+        t_val = torch.from_numpy(val).to(dev)
+        x = torch.from_numpy(W.uniform_vector(n, W.rng_for(4, 1))).to(dev)
+        y = torch.empty(n, dtype=torch.float64, device=dev)
+        plan = D.Plan(t_rp, nnz, n, torch.float64, idx=off)
+        plan.set_tiling(D.DAMN_TILING_ROWS_LONG)
+        for _ in range(args.steps):
+            D.damn_spmv_dacsr16(t_rp, off, t_val, x, y, plan=plan)
+    else:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(W.seed_for(5, 1))
+        mats = []
+        for n, rp, col, val in W.batch_banded(512):
+            t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
+            off, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
+            X = torch.rand((n, 1), generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+            Y = torch.empty((n, 1), dtype=torch.float64, device=dev)
+            mats.append((t_rp, off, torch.from_numpy(val).to(dev), X, Y))
+        plan = D.BatchPlan(mats, 1, torch.float64, autotune=False)
+        for _ in range(args.steps):
+            plan.launch()
+    torch.cuda.synchronize()
+    if D.damn_device_status() != 0:
+        raise RuntimeError("device status word reports an error")
+    print(json.dumps({"case": args.case, "launches": args.steps}), flush=True)
+
+
 # ----------------------------------------------------------------------------
 # secondary sections
 # ----------------------------------------------------------------------------
@@ -671,6 +720,8 @@ def main():
                     help="parts (streams) each end-to-end upload / download is split into")
     ap.add_argument("--tiling", default="auto", choices=["auto", "rows", "rows_long", "slices"],
                     help="headline plan tiling: autotuned, or fixed")
+    ap.add_argument("--case", default=None, choices=PROFILE_CASES,
+                    help="run only the launches of one profiled kernel (for ncu), no timing")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -679,6 +730,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.case:
+        run_case(args)
         return
 
     import torch
