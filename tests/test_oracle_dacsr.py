@@ -19,7 +19,7 @@ def test_example1(golden):
     # the generator's copy of Fig. 1 is the same pattern
     rp, c, _ = W.example1_pattern()
     assert rp.tolist() == rowptr.tolist() and c.tolist() == col.tolist()
-    # "colids covers its full range": [0, ncols-1] for CSR, [-w, w] for DA-CSR
+    # Example 1: the stored indices span [0, ncols-1] in CSR and [-w, w] in DA-CSR
     assert (col.min(), col.max()) == (0, n - 1)
     assert (off.min(), off.max()) == (-info.w, info.w)
 
