@@ -1,9 +1,9 @@
 """y <- alpha A x + beta y for CSR and DA-CSR storage (Section 4, Listing 2).
 Test infrastructure only (see ``oracle/__init__.py``).
 
-Listing 2 walks the rows in order; for each row it starts an accumulator at
-zero, adds value * x[col] for the row's entries in stored order, and finally
-stores alpha * accumulator + beta * y[row].  DA-CSR reads x through a view
+Listing 2 walks the rows in order.  Each row's sum starts at zero and takes
+value * x[col] for the row's entries in stored order; the row's output is
+then alpha times that sum, plus beta times the old y entry.  DA-CSR reads x through a view
 shifted by the row, so an entry with stored index ``off`` multiplies
 x[row + off]; CSR reads x[col] directly.  Both variants compute the same
 numbers in the same order.
