@@ -105,3 +105,44 @@ def test_struct_layouts_match_c(tmp_path):
         assert ctypes.sizeof(cls) == c[(s, "size")], s
         for f, _ in cls._fields_:
             assert getattr(cls, f).offset == c[(s, f)], (s, f)
+
+
+def test_plain_c_program_links_and_calls(tmp_path):
+    """A plain C program (no C++, no Python) includes damn.h, links
+    libdamn.so and calls host-side entry points: the library is usable
+    through its C ABI alone."""
+    import subprocess
+    from paper_2307_06305_gb300 import build
+    path = build.build()
+    src = tmp_path / "use_damn.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <stdint.h>
+#include "damn.h"
+int main(void) {
+  /* path 0-1-2-3-4 relabelled as 2-0-4-1-3 (diagonal entries included) */
+  const int32_t rowptr[6] = {0, 3, 6, 8, 10, 13};
+  const int32_t col[13] = {0, 2, 4, 1, 3, 4, 0, 2, 1, 3, 0, 1, 4};
+  int32_t perm[5];
+  int64_t wb = -1, wa = -1;
+  int rc = damn_rcm_order(5, 13, rowptr, col, perm, &wb, &wa);
+  if (rc != DAMN_OK) { printf("rcm rc %d %s\n", rc, damn_last_error()); return 1; }
+  printf("perm %d %d %d %d %d w %lld %lld\n", perm[0], perm[1], perm[2], perm[3], perm[4],
+         (long long)wb, (long long)wa);
+  rc = damn_spmv_dacsr16(-1, 1, 0, NULL, NULL, NULL, DAMN_F64, NULL, NULL, 1.0, 0.0, NULL, NULL);
+  printf("spmv rc %d %s\n", rc, damn_last_error());
+  printf("version %d\n", damn_version());
+  return rc == DAMN_ERR_INVALID_ARG ? 0 : 2;
+}
+""")
+    exe = tmp_path / "use_damn"
+    libdir = os.path.dirname(path)
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", libdir, "-ldamn", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout + out.stderr
+    lines = out.stdout.splitlines()
+    # the hand-worked RCM of this path (tests/golden/rcm_hand_examples.txt)
+    # numbers it along the path: bandwidth 4 before, 1 after
+    assert lines[0] == "perm 3 1 4 0 2 w 4 1", lines[0]
+    assert lines[1].startswith("spmv rc -1 damn_spmv_dacsr16")
