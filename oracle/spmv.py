@@ -93,20 +93,6 @@ def spmv(nrows: int, rowptr, idx, val, x, y=None, alpha=1.0, beta=0.0,
     return (t(alpha) * acc + t(beta) * np.asarray(y).astype(dtype)).astype(dtype)
 
 
-def spmv_rows_subset(rows, rowptr, idx, val, x, y=None, alpha=1.0, beta=0.0,
-                     diagonal_addressed: bool = True) -> np.ndarray:
-    """Listing 2 for selected rows only (FP64), for spot checks of large
-    matrices."""
-    out = np.zeros(len(rows))
-    for k, row in enumerate(np.asarray(rows, dtype=np.int64).tolist()):
-        acc = 0.0
-        for i in range(int(rowptr[row]), int(rowptr[row + 1])):
-            c = row + int(idx[i]) if diagonal_addressed else int(idx[i])
-            acc = acc + float(val[i]) * float(x[c])
-        out[k] = alpha * acc if beta == 0 else alpha * acc + beta * float(y[row])
-    return out
-
-
 def spmv_exact(nrows: int, rowptr, idx, val, x, y=None, alpha=1.0, beta=0.0,
                diagonal_addressed: bool = True, rows=None) -> np.ndarray:
     """alpha A x + beta y in exact rational arithmetic, rounded once to FP64

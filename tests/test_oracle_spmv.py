@@ -212,3 +212,140 @@ def test_planted_mistakes_are_caught(mistake, monkeypatch):
     dense = a * (A @ x) + b * y
     bnd = S.error_bound(nr, rp, off, v, x, y, a, b)
     assert np.any(np.abs(got - dense) > 2 * bnd)
+
+
+# --------------------------------------------------------------------------
+# error_bound: exact values on a hand-worked matrix.  The tolerance of every
+# random-input GPU test is this function, so it is pinned to the formula of
+# the componentwise bound written out with the numbers of a small example:
+#
+#   alpha = 1, beta = 0:  4 * len * u * S + len * tiny
+#   otherwise:            4 * (len + 2) * u * (|alpha| S + |beta| |y0|) + (len + 2) * tiny
+#
+# with S = sum_j |a_rj x_j|, len the row's stored entries, u the unit
+# roundoff of the accumulation type and tiny its smallest normal number.
+# --------------------------------------------------------------------------
+TINY64 = 2.0 ** -1022
+TINY32 = 2.0 ** -126
+
+
+def _bound_example():
+    # 3 x 4 matrix, row 1 empty:
+    #   row 0: a = (1 at col 0, -2 at col 2)             S = |1*3| + |-2*0.5|          = 4,    len 2
+    #   row 2: a = (0.25 at col 1, 8 at col 2, -1 at col 3)
+    #                                        S = |0.25*5| + |8*0.5| + |-1*-4| = 9.25, len 3
+    rp = np.array([0, 2, 2, 5], dtype=np.int32)
+    col = np.array([0, 2, 1, 2, 3], dtype=np.int32)
+    val = np.array([1.0, -2.0, 0.25, 8.0, -1.0])
+    x = np.array([3.0, 5.0, 0.5, -4.0])
+    y0 = np.array([2.0, -1.0, 0.5])
+    return rp, col, val, x, y0
+
+
+def _bound_pin_failures(bound_fn):
+    """Cases where bound_fn differs from the hand-computed bound (empty list:
+    the pin holds)."""
+    rp, col, val, x, y0 = _bound_example()
+    off = D.translate(3, rp, col)
+    cases = []
+    for u, tiny in ((S.U64, TINY64), (S.U32, TINY32)):
+        # alpha = 1, beta = 0
+        cases.append((dict(u=u), [4 * 2 * u * 4 + 2 * tiny, 0.0, 4 * 3 * u * 9.25 + 3 * tiny]))
+        # alpha = 0.5, beta = -3, y0 = (2, -1, 0.5)
+        cases.append((dict(y=y0, alpha=0.5, beta=-3.0, u=u),
+                      [4 * 4 * u * (0.5 * 4 + 3 * 2) + 4 * tiny,
+                       4 * 2 * u * (0.0 + 3 * 1) + 2 * tiny,
+                       4 * 5 * u * (0.5 * 9.25 + 3 * 0.5) + 5 * tiny]))
+        # alpha = -2, beta = 0 (general branch without the y term)
+        cases.append((dict(alpha=-2.0, u=u),
+                      [4 * 4 * u * (2 * 4) + 4 * tiny, 2 * tiny,
+                       4 * 5 * u * (2 * 9.25) + 5 * tiny]))
+    bad = []
+    for kw, expect in cases:
+        for idx, da in ((off, True), (col, False)):
+            kw2 = dict(kw)
+            got = bound_fn(3, rp, idx, val, x, kw2.pop("y", None), kw2.pop("alpha", 1.0),
+                           kw2.pop("beta", 0.0), diagonal_addressed=da, **kw2)
+            if not np.allclose(got, expect, rtol=1e-14, atol=0.0):
+                bad.append((kw, da, list(got), expect))
+    # subnormal products: S = 2^-1060 is below the normal range, the relative
+    # term underflows and the absolute term len * tiny is the whole bound
+    rp1 = np.array([0, 1], dtype=np.int32)
+    got = bound_fn(1, rp1, np.array([0]), np.array([2.0 ** -1000]), np.array([2.0 ** -60]),
+                   diagonal_addressed=False)
+    if not np.allclose(got, [TINY64], rtol=1e-14, atol=0.0):
+        bad.append(("subnormal", list(got), [TINY64]))
+    return bad
+
+
+def test_error_bound_hand_values():
+    assert _bound_pin_failures(S.error_bound) == []
+
+
+def _slipped(kind):
+    """error_bound with one plausible slip planted (for the test below)."""
+    def fn(nrows, rowptr, idx, val, x, y=None, alpha=1.0, beta=0.0,
+           diagonal_addressed=True, u=S.U64):
+        lens = np.diff(np.asarray(rowptr, dtype=np.int64)).astype(np.float64)
+        if kind == "total_nnz":
+            lens = np.full_like(lens, float(rowptr[-1]))
+        s = S.abs_row_sums(nrows, rowptr, idx, val, x, diagonal_addressed)
+        if kind == "abs_of_sum":
+            cols = (D.entry_rows(nrows, rowptr) + np.asarray(idx)) if diagonal_addressed \
+                else np.asarray(idx)
+            s = np.abs(np.bincount(D.entry_rows(nrows, rowptr),
+                                   weights=np.asarray(val) * np.asarray(x)[cols],
+                                   minlength=nrows))
+        uu = S.U32 if (kind == "u_swapped" and u == S.U64) else u
+        tiny = np.finfo(np.float64 if u == S.U64 else np.float32).tiny
+        if kind == "no_tiny":
+            tiny = 0.0
+        k = 40.0 if kind == "factor_10" else 4.0
+        if alpha == 1.0 and beta == 0.0 and kind != "plus2_always":
+            return k * lens * uu * s + lens * tiny
+        yabs = np.abs(np.asarray(y, dtype=np.float64)) if beta != 0 else 0.0
+        if kind == "beta_dropped":
+            yabs = 0.0
+        return k * (lens + 2.0) * uu * (abs(alpha) * s + abs(beta) * yabs) + (lens + 2.0) * tiny
+    return fn
+
+
+@pytest.mark.parametrize("kind", ["u_swapped", "total_nnz", "factor_10", "plus2_always",
+                                  "beta_dropped", "abs_of_sum", "no_tiny"])
+def test_error_bound_pin_catches_slips(kind):
+    """Each slip -- a looser or a tighter bound -- fails the hand-value pin."""
+    assert _bound_pin_failures(_slipped(kind)) != []
+
+
+def test_error_bound_accepts_and_rejects_at_its_edge():
+    """A result 8 ulps from the exact value of a row sum 2 with bound
+    32 * 2^-53 = 8 ulps(2) is accepted; 9 ulps is rejected, as a GPU result
+    just outside the stated tolerance must be."""
+    rp, col, val, x, _ = _bound_example()
+    off = D.translate(3, rp, col)
+    ex = S.spmv_exact(3, rp, off, val, x)
+    bnd = S.error_bound(3, rp, off, val, x)
+    assert ex[0] == 2.0 and bnd[0] == 8 * np.spacing(2.0)
+    y = ex.copy()
+    for _ in range(8):
+        y[0] = np.nextafter(y[0], np.inf)
+    assert np.all(np.abs(y - ex) <= bnd)
+    y[0] = np.nextafter(y[0], np.inf)
+    assert not np.all(np.abs(y - ex) <= bnd)
+
+
+def test_recursive_summation_error_reaches_a_quarter_of_the_bound():
+    """The bound is not loose by more than its factor 4: left-to-right
+    summation of 1 + u + u + ... (every partial sum rounds back to 1, ties to
+    even) loses (len - 1) u, a quarter of 4 len u S up to O(1/len)."""
+    n = 1001
+    rp = np.array([0, n], dtype=np.int32)
+    val = np.concatenate([[1.0], np.full(n - 1, S.U64)])
+    x = np.ones(n)
+    col = np.arange(n, dtype=np.int32)
+    got = S.spmv(1, rp, col, val, x, diagonal_addressed=False)
+    ex = S.spmv_exact(1, rp, col, val, x, diagonal_addressed=False)
+    bnd = S.error_bound(1, rp, col, val, x, diagonal_addressed=False)
+    assert got[0] == 1.0
+    err = abs(got[0] - ex[0])
+    assert err <= bnd[0] and err >= 0.24 * bnd[0]
