@@ -86,6 +86,8 @@ int damn_selftest_wait_timeout(int64_t timeout_ns, void *stream);
 /* a1: CSR -> DA-CSR-16 translation and fit check (Section 2, Example 1,     */
 /*     Eq. (2); fit reading: every c - r in [-32768, 32767])                 */
 /* ------------------------------------------------------------------------ */
+/* min_off and max_off saturate at the int32 limits; only columns outside
+ * [0, ncols) can reach them (then n_bad > 0 and fits == 0). */
 typedef struct {
   int32_t min_off;  /* smallest c - r over stored entries (0 if nnz == 0)      */
   int32_t max_off;  /* largest c - r (0 if nnz == 0)                            */
@@ -110,7 +112,7 @@ int damn_csr_to_dacsr(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *
                       void *workspace, size_t ws_bytes, void *stream);
 
 /* Same with 8-bit offsets (DA-CSR-8; the int8 index width of the traffic
- * lattice of Section 3, Fig. 3): off_out[i] = col[i] - r_i narrowed to
+ * lattice of Section 2, Fig. 3): off_out[i] = col[i] - r_i narrowed to
  * int8, fits iff every offset lies in [-128, 127] (h_info->n_fit counts the
  * entries in that range).  Same workspace and errors as damn_csr_to_dacsr. */
 int damn_csr_to_dacsr8(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
@@ -126,10 +128,13 @@ int damn_csr_to_dacsr8(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t 
  * the library (about 64 KiB on every device that loads the library, held until
  * the process exits), which limits nrows to DAMN_NOALLOC_MAX_ROWS; larger
  * matrices are rejected with DAMN_ERR_INVALID_ARG.  The first call on a device
- * looks up the array's device address, so make that first call before any
- * stream capture.  Every call uses the same array: calls that overlap on the
- * GPU (other streams or host threads without ordering between them) race.
- * Synchronises stream; calls no allocator. */
+ * looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture; the lookup is repeated once after a
+ * device reset, which gives the device a new context.  Every call uses the
+ * same array and leaves its last contents there (each call overwrites every
+ * record it reads): calls that overlap on the GPU (other streams or host
+ * threads without ordering between them) race.  The call waits for stream to
+ * finish (it reads the fit result back to *h_info); it calls no allocator. */
 #define DAMN_NOALLOC_MAX_ROWS 1048576
 int damn_csr_to_dacsr_noalloc(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
                               const int32_t *col, int16_t *off_out, damn_fit_info *h_info,

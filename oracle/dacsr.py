@@ -11,7 +11,7 @@ admits 16-bit indices (Example 2, Section 3).  The oracle declares a matrix to
 fit iff every translated index lies in [-32768, 32767], the range a signed
 16-bit integer holds; this differs from "w < 2^15" only when the most negative
 offset is exactly -32768.  The same rule with 8 bits ([-128, 127]) gives
-DA-CSR-8, the int8 index width of the traffic lattice (Section 3, Fig. 3).
+DA-CSR-8, the int8 index width of the traffic lattice (Section 2, Fig. 3).
 """
 from __future__ import annotations
 

@@ -342,6 +342,8 @@ extern "C" int damn_cg(int32_t n, int64_t nnz, const int32_t *rowptr, const int1
   int rc = check_cg_args("damn_cg", n, nnz, rowptr, off, val, b, x, h_res, workspace, ws_bytes,
                          damn_cg_workspace_size(n));
   if (rc) return rc;
+  rc = plan_check("damn_cg", plan, DAMN_FMT_DACSR16, n, n, nnz, rowptr, off, DAMN_F64);
+  if (rc) return rc;
   std::memset(h_res, 0, sizeof(*h_res));
   if (n == 0) { h_res->converged = 1; return DAMN_OK; }
   if (!(rtol > 0) || max_iter < 0) return set_error(DAMN_ERR_INVALID_ARG, "damn_cg: bad rtol / max_iter");
@@ -381,6 +383,9 @@ extern "C" int damn_cg(int32_t n, int64_t nnz, const int32_t *rowptr, const int1
   h_res->relres = std::sqrt(h.rr[iters & 1] / (bb > 0 ? bb : 1.0));
   rc = true_relres(A, b, x, r, part_a, tmp, s, &h_res->true_relres);
   if (rc) return rc;
+  // a bounded wait that gave up inside an SpMV left vectors partly computed
+  rc = check_device_status(s, "damn_cg");
+  if (rc) return rc;
   if (done == 2) return set_error(DAMN_ERR_NOT_CONVERGED, "damn_cg: breakdown (p.q <= 0)");
   if (!h_res->converged)
     return set_error(DAMN_ERR_NOT_CONVERGED, "damn_cg: not converged after %d iterations", iters);
@@ -407,6 +412,10 @@ extern "C" int damn_cg_ir(int32_t n, int64_t nnz, const int32_t *rowptr, const i
   if (nnz > 0 && !val_low) return set_error(DAMN_ERR_INVALID_ARG, "damn_cg_ir: val_low is NULL");
   if (!(rtol > 0) || !(inner_rtol > 0) || max_inner < 1 || max_outer < 0)
     return set_error(DAMN_ERR_INVALID_ARG, "damn_cg_ir: bad tolerances or iteration caps");
+  rc = plan_check("damn_cg_ir", plan64, DAMN_FMT_DACSR16, n, n, nnz, rowptr, off, DAMN_F64);
+  if (rc) return rc;
+  rc = plan_check("damn_cg_ir", plan_low, DAMN_FMT_DACSR16, n, n, nnz, rowptr, off, low_dtype);
+  if (rc) return rc;
   std::memset(h_res, 0, sizeof(*h_res));
   if (n == 0) { h_res->converged = 1; return DAMN_OK; }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -444,7 +453,10 @@ extern "C" int damn_cg_ir(int32_t n, int64_t nnz, const int32_t *rowptr, const i
     DAMN_CHECK_LAUNCH("cg_ir residual");
     double rr = 0;
     DAMN_CUDA(cudaMemcpyAsync(&rr, tmp, sizeof(double), cudaMemcpyDeviceToHost, s));
-    DAMN_CUDA(cudaStreamSynchronize(s));
+    // also synchronises: a bounded wait that gave up inside an SpMV (this
+    // residual or the previous inner solve) left vectors partly computed
+    rc = check_device_status(s, "damn_cg_ir");
+    if (rc) return rc;
     relres = std::sqrt(rr) / nb;
     if (relres <= rtol) { converged = true; break; }
     if (outer >= max_outer || !std::isfinite(relres)) break;

@@ -1,5 +1,7 @@
 // Library-wide host state: error messages, the device status word, the
 // failure-detection self test, version.
+#include <cuda.h>
+
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
@@ -16,10 +18,71 @@ thread_local std::string g_last_error;
 __device__ int g_status_word;
 
 constexpr int kMaxDevices = 64;
-int *g_status_ptr[kMaxDevices];
+SymbolCache g_status_cache;
 int g_sm_count[kMaxDevices];
 std::mutex g_mu;
+
+using PfnCtxGetCurrent = CUresult (*)(CUcontext *);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long *);
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+std::once_flag g_ctx_fn_once;
 }  // namespace
+
+unsigned long long context_id() {
+  std::call_once(g_ctx_fn_once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get_current = reinterpret_cast<PfnCtxGetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get_id = reinterpret_cast<PfnCtxGetId>(f);
+  });
+  if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  unsigned long long id = 0;
+  if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+void *symbol_address(SymbolCache &cache, const void *symbol, const char *what, int *rc) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) { *rc = cuda_error(e, what); return nullptr; }
+  if (dev < 0 || dev >= SymbolCache::kDevices) {
+    *rc = set_error(DAMN_ERR_UNSUPPORTED, "%s: device index %d", what, dev);
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(cache.mu);
+  const unsigned long long ctx = context_id();
+  if (!cache.addr[dev] || ctx == 0 || cache.ctx[dev] != ctx) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, symbol);
+    if (e != cudaSuccess) { *rc = cuda_error(e, what); return nullptr; }
+    cache.addr[dev] = p;
+    cache.ctx[dev] = context_id();  // the lookup above created the context if needed
+  }
+  return cache.addr[dev];
+}
+
+int check_device_status(cudaStream_t s, const char *what) {
+  int *p = device_status_ptr();
+  if (!p) return set_error(DAMN_ERR_CUDA, "%s: no device status word", what);
+  int v = 0;
+  DAMN_CUDA(cudaMemcpyAsync(&v, p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DAMN_CUDA(cudaStreamSynchronize(s));
+  if (v != DAMN_OK)
+    return set_error(v, "%s: the device status word reports %d (a bounded device-side wait gave "
+                        "up, or a device-side check failed); results are incomplete",
+                     what, v);
+  return DAMN_OK;
+}
 
 int set_error(int code, const char *fmt, ...) {
   char buf[512];
@@ -36,15 +99,8 @@ int cuda_error(cudaError_t e, const char *what) {
 }
 
 int *device_status_ptr() {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_status_ptr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
-    g_status_ptr[dev] = static_cast<int *>(p);
-  }
-  return g_status_ptr[dev];
+  int rc = DAMN_OK;
+  return static_cast<int *>(symbol_address(g_status_cache, &g_status_word, "device status word", &rc));
 }
 
 int sm_count() {

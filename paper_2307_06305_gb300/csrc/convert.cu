@@ -43,6 +43,12 @@ __device__ __forceinline__ int row_of(const int *rp, int nr, int k) {
   return lo;
 }
 
+// c - r saturated to the int32 range of the reported min / max offsets
+// (reached only by columns outside [0, ncols)).
+__device__ __forceinline__ int sat_int(long long d) {
+  return static_cast<int>(d < INT_MIN ? (long long)INT_MIN : d > INT_MAX ? (long long)INT_MAX : d);
+}
+
 template <int NT>
 __device__ __forceinline__ void block_reduce_fit(int mn, int mx, unsigned long long nf,
                                                  unsigned long long nb, FitAccum *acc) {
@@ -88,10 +94,11 @@ k_csr_to_dacsr(int nrows, int ncols, const int *__restrict__ rowptr, const int *
   for (int k = k0 + threadIdx.x; k < k1; k += kConvThreads) {
     const int lr = row_of(rp, nr, k);
     const int c = __ldcs(col + k);
-    const int d = c - (r0 + lr);  // |d| < 2^31 since 0 <= r, c < 2^31
+    // in 64 bits: a bad column near INT_MIN would overflow c - r in int32
+    const long long d = (long long)c - (r0 + lr);
     off[k] = static_cast<OffT>(d);
-    mn = min(mn, d);
-    mx = max(mx, d);
+    mn = min(mn, sat_int(d));
+    mx = max(mx, sat_int(d));
     nf += (d >= kLo && d <= kHi) ? 1ull : 0ull;
     nb += (c < 0 || c >= ncols) ? 1ull : 0ull;
   }
@@ -309,10 +316,10 @@ k_csr_to_dacsr16_part(int nrows, int ncols, const int *__restrict__ rowptr,
   for (int k = k0 + threadIdx.x; k < k1; k += kConvThreads) {
     const int lr = row_of(rp, nr, k);
     const int c = __ldcs(col + k);
-    const int d = c - (r0 + lr);
+    const long long d = (long long)c - (r0 + lr);  // 64 bits, as above
     __stcs(off + k, static_cast<int16_t>(d));
-    mn = min(mn, d);
-    mx = max(mx, d);
+    mn = min(mn, sat_int(d));
+    mx = max(mx, sat_int(d));
     nf += (d >= -32768 && d <= 32767) ? 1ull : 0ull;
     nb += (c < 0 || c >= ncols) ? 1ull : 0ull;
   }
@@ -367,30 +374,15 @@ __global__ void k_fit_reduce_part(const FitPartial *part, int nblocks, FitPartia
   }
 }
 
-// Device address of g_noalloc_fit on the current device, looked up once per
-// device.  In host code the array's name is only a stand-in for the symbol,
-// so kernels get this address, never the name.
+// Device address of g_noalloc_fit on the current device, looked up with
+// cudaGetSymbolAddress once per device (again after a device reset, which
+// gives the device a new context).  In host code the array's name is only a
+// stand-in for the symbol, so kernels get this address, never the name.
+SymbolCache g_noalloc_cache;
+
 FitPartial *noalloc_fit_scratch(int *rc) {
-  static FitPartial *addr[64];
-  static std::mutex mu;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) { *rc = cuda_error(e, "damn_csr_to_dacsr_noalloc: cudaGetDevice"); return nullptr; }
-  if (dev < 0 || dev >= 64) {
-    *rc = set_error(DAMN_ERR_UNSUPPORTED, "damn_csr_to_dacsr_noalloc: device index %d", dev);
-    return nullptr;
-  }
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_fit);
-    if (e != cudaSuccess) {
-      *rc = cuda_error(e, "damn_csr_to_dacsr_noalloc: cudaGetSymbolAddress");
-      return nullptr;
-    }
-    addr[dev] = static_cast<FitPartial *>(p);
-  }
-  return addr[dev];
+  return static_cast<FitPartial *>(symbol_address(g_noalloc_cache, &g_noalloc_fit,
+                                                  "damn_csr_to_dacsr_noalloc: scratch address", rc));
 }
 
 }  // namespace

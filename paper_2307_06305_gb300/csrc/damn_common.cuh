@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <mutex>
 #include <string>
 
 #include "../../include/damn.h"
@@ -22,6 +23,31 @@ int set_error(int code, const char *fmt, ...);
 int cuda_error(cudaError_t e, const char *what);
 int *device_status_ptr();          // library status word on the current device
 int sm_count();                    // SMs of the current device
+
+// Identifier of the calling thread's current CUDA context, 0 when there is
+// none yet.  A device reset destroys the context and its successor gets a new
+// identifier.
+unsigned long long context_id();
+
+// Device addresses of one __device__ variable, one per device, each valid for
+// the context it was looked up in.
+struct SymbolCache {
+  static constexpr int kDevices = 64;
+  unsigned long long ctx[kDevices] = {};
+  void *addr[kDevices] = {};
+  std::mutex mu;
+};
+
+// Device address of `symbol` (the host-side stand-in of a __device__
+// variable) on the current device: cudaGetSymbolAddress once per device
+// context, cached in `cache`.  A kernel must be given this address, never
+// the stand-in.  NULL on failure (*rc set).
+void *symbol_address(SymbolCache &cache, const void *symbol, const char *what, int *rc);
+
+// Reads the device status word (synchronises s): DAMN_OK, or the recorded
+// error code (with a message) when a bounded wait gave up or a device-side
+// check failed.  The word is not cleared.
+int check_device_status(cudaStream_t s, const char *what);
 
 #define DAMN_CUDA(call)                                                  \
   do {                                                                   \

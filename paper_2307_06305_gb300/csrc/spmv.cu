@@ -423,11 +423,29 @@ int spmv_launch(const SpmvCall &c, const damn_plan *plan, cudaStream_t s, int *g
   return rc;
 }
 
+int plan_check(const char *fn, const damn_plan *plan, int fmt, int32_t nrows, int32_t ncols,
+               int64_t nnz, const int32_t *rowptr, const void *idx, int dtype) {
+  if (!plan) return DAMN_OK;
+  if (plan->nrows != nrows || plan->ncols != ncols || plan->nnz != nnz || plan->dtype != dtype)
+    return set_error(DAMN_ERR_INVALID_ARG, "%s: plan was built for another matrix or dtype", fn);
+  // The plan's tiles and x windows were computed from its own rowptr and
+  // index array: a call with other arrays of the same sizes would read rows
+  // and x slots the plan never prepared.  The same matrix in another index
+  // format (CSR-32 col for a plan built from DA-CSR offsets, or the reverse)
+  // is the documented exception.
+  if (nrows > 0 && plan->rowptr != rowptr)
+    return set_error(DAMN_ERR_INVALID_ARG, "%s: rowptr is not the array the plan was built from", fn);
+  if (plan->idx && plan->fmt == fmt && plan->idx != idx)
+    return set_error(DAMN_ERR_INVALID_ARG,
+                     "%s: index array is not the one the plan was built from", fn);
+  return DAMN_OK;
+}
+
 }  // namespace damn
 
 using namespace damn;
 
-static int check_spmv_args(const char *fn, int32_t nrows, int32_t ncols, int64_t nnz,
+static int check_spmv_args(const char *fn, int fmt, int32_t nrows, int32_t ncols, int64_t nnz,
                            const int32_t *rowptr, const void *idx, const void *val, int dtype,
                            const void *x, void *y, const damn_plan *plan) {
   if (nrows < 0 || ncols < 0 || nnz < 0 || nnz > INT_MAX)
@@ -438,17 +456,14 @@ static int check_spmv_args(const char *fn, int32_t nrows, int32_t ncols, int64_t
   if (nnz > 0 && (!idx || !val || !x)) return set_error(DAMN_ERR_INVALID_ARG, "%s: NULL pointer", fn);
   if (!aligned16(rowptr) || !aligned16(idx) || !aligned16(val) || !aligned16(x) || !aligned16(y))
     return set_error(DAMN_ERR_INVALID_ARG, "%s: pointers must be 16-byte aligned", fn);
-  if (plan && (plan->nrows != nrows || plan->ncols != ncols || plan->nnz != nnz ||
-               plan->dtype != dtype))
-    return set_error(DAMN_ERR_INVALID_ARG, "%s: plan was built for another matrix or dtype", fn);
-  return DAMN_OK;
+  return plan_check(fn, plan, fmt, nrows, ncols, nnz, rowptr, idx, dtype);
 }
 
 static int spmv_entry(const char *fn, int fmt, int32_t nrows, int32_t ncols, int64_t nnz,
                       const int32_t *rowptr, const void *idx, const void *val, int dtype,
                       const void *x, void *y, double alpha, double beta, const damn_plan *plan,
                       void *stream) {
-  int rc = check_spmv_args(fn, nrows, ncols, nnz, rowptr, idx, val, dtype, x, y, plan);
+  int rc = check_spmv_args(fn, fmt, nrows, ncols, nnz, rowptr, idx, val, dtype, x, y, plan);
   if (rc) return rc;
   if (nrows == 0) return DAMN_OK;
   SpmvCall c;
@@ -627,8 +642,8 @@ extern "C" int damn_plan_autotune(damn_plan *plan, int format, const void *idx, 
   if (!plan) return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_autotune: plan is NULL");
   if (format != DAMN_FMT_CSR32 && format != DAMN_FMT_DACSR16 && format != DAMN_FMT_DACSR8)
     return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_autotune: bad format");
-  int rc = check_spmv_args("damn_plan_autotune", plan->nrows, plan->ncols, plan->nnz, plan->rowptr,
-                           idx, val, plan->dtype, x, y, plan);
+  int rc = check_spmv_args("damn_plan_autotune", format, plan->nrows, plan->ncols, plan->nnz,
+                           plan->rowptr, idx, val, plan->dtype, x, y, plan);
   if (rc) return rc;
   if (plan->nrows == 0) return DAMN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

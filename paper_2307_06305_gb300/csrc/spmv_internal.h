@@ -37,4 +37,11 @@ int spmv_launch(const SpmvCall &c, const damn_plan *plan, cudaStream_t s, int *g
 // Upper bound of the number of CTAs (dot partials) spmv_launch may use.
 int spmv_max_grid();
 
+// DAMN_OK when plan is NULL or was built for this matrix: same sizes and
+// dtype, the same rowptr array, and the same index array when fmt is the
+// plan's own format (another format's copy of the same matrix is allowed).
+// Otherwise DAMN_ERR_INVALID_ARG with a message naming fn.
+int plan_check(const char *fn, const damn_plan *plan, int fmt, int32_t nrows, int32_t ncols,
+               int64_t nnz, const int32_t *rowptr, const void *idx, int dtype);
+
 }  // namespace damn

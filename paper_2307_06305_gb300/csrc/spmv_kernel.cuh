@@ -165,6 +165,7 @@ struct Layout {
   static constexpr size_t V_BYTES = align_up((C::CAP_NZ + 2 * EV) * sizeof(V), 128);
   static constexpr size_t I_BYTES = align_up((C::CAP_NZ + 2 * EI) * sizeof(I), 128);
   static constexpr size_t X_BYTES = align_up((XCAP + 2 * kXSegMax * EX) * sizeof(A), 128);
+  static constexpr int X_ELEMS = static_cast<int>(X_BYTES / sizeof(A));  // slots of the x buffer
   static constexpr size_t OFF_V = RP_BYTES, OFF_I = RP_BYTES + V_BYTES,
                           OFF_X = RP_BYTES + V_BYTES + I_BYTES;
   static constexpr size_t STAGE = OFF_X + X_BYTES;
@@ -392,7 +393,11 @@ __device__ __forceinline__ void produce(const SpmvParams &p, unsigned char *smem
 //   slot(cl) = cl + e_0 + [cl >= lo_1] (e_1 - e_0) + [cl >= lo_2] (e_2 - e_1) + ...
 // Unused segments have lo = INT_MAX: no branch and no indexing by a runtime
 // segment number.  For DA-CSR the tile-local column of row r0 + i is simply
-// i + off.
+// i + off.  The slot is clamped (one unsigned min) to the x buffer of XL
+// elements, so that a column the plan did not see (a call whose pattern is
+// not the plan's) reads a wrong value inside the stage instead of shared
+// memory outside it.
+template <int XL>
 struct XMap {
   int d0, lo1, lo2, lo3, dd1, dd2, dd3;
   __device__ __forceinline__ void load(const TileHdr &h) {
@@ -400,9 +405,7 @@ struct XMap {
     const int4 b = hv[1], c = hv[2], d = hv[3];
     d0 = b.w; lo1 = c.x; lo2 = c.y; lo3 = c.z; dd1 = c.w; dd2 = d.x; dd3 = d.y;
   }
-  __device__ __forceinline__ int slot(int cl) const {
-    return cl + d0 + (cl >= lo1 ? dd1 : 0) + (cl >= lo2 ? dd2 : 0) + (cl >= lo3 ? dd3 : 0);
-  }
+  __device__ __forceinline__ int slot(int cl) const { return slot_n<kXSegMax>(cl); }
   // the same when the window has at most NS segments
   template <int NS>
   __device__ __forceinline__ int slot_n(int cl) const {
@@ -410,7 +413,7 @@ struct XMap {
     if (NS > 1) r += cl >= lo1 ? dd1 : 0;
     if (NS > 2) r += cl >= lo2 ? dd2 : 0;
     if (NS > 3) r += cl >= lo3 ? dd3 : 0;
-    return r;
+    return static_cast<int>(min(static_cast<unsigned>(r), static_cast<unsigned>(XL - 1)));
   }
 };
 
@@ -461,8 +464,8 @@ struct TileView {
 
 // x value of column c of a tile starting at row r0: from the staged window or
 // gathered from global memory.
-template <typename A>
-__device__ __forceinline__ A x_at(const A *xg, const A *xs, const XMap &xm, bool staged, int c,
+template <typename A, class XM>
+__device__ __forceinline__ A x_at(const A *xg, const A *xs, const XM &xm, bool staged, int c,
                                   int r0) {
   return staged ? xs[xm.slot(c - r0)] : ldg(xg + c);
 }
@@ -478,7 +481,7 @@ __device__ __noinline__ void rows_general(const SpmvParams &p, unsigned char *sm
   constexpr bool DA = sizeof(I) < 4;  // int16 / int8 offsets
   TileView<V, I, C> tv;
   tv.init(p, smem, h, s);
-  XMap xm;
+  XMap<Layout<V, I, C>::X_ELEMS> xm;
   const bool staged = (h.flags & kTileStaged) != 0;
   if (staged) xm.load(h);
   const A *xg = static_cast<const A *>(p.x);
@@ -520,7 +523,7 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
       continue;
     }
     const int4 h1 = hv[1];  // rp_sh, v_sh, i_sh, d0
-    XMap xm;
+    XMap<L::X_ELEMS> xm;
     xm.load(hdr[s]);
     unsigned char *st = smem + (size_t)s * L::STAGE;
     const int *rp = reinterpret_cast<const int *>(st) + h1.x;
@@ -599,7 +602,7 @@ __device__ __forceinline__ void tile_slices(const SpmvParams &p, const TileHdr &
   const int *rp = tv.rp;
   const int nr = h.nr, m = h.m, k0 = h.k0;
   const bool staged = (h.flags & kTileStaged) != 0;
-  XMap xm;
+  XMap<Layout<V, I, C>::X_ELEMS> xm;
   if (staged) xm.load(h);
   const int K = m > 0 ? (m + C::NT - 1) / C::NT : 0;
   const int s = ctid * K;

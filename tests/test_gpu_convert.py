@@ -64,6 +64,30 @@ def test_empty_rows_nonsquare_and_bad_columns(D, cuda_dev):
     assert info.n_bad == 2 and not info.fits
 
 
+def test_bad_column_near_int_min(D, cuda_dev):
+    """c - r is formed in 64 bits: a column of -2^31 in row 5 gives c - r =
+    -2^31 - 5, which the int32 min_off reports saturated at -2^31; the
+    counts and the fit decision are exact."""
+    n = 700
+    rows = np.append(np.arange(n), [5, 600])
+    cols = np.append(np.arange(n), [-2 ** 31, 2 ** 31 - 1]).astype(np.int64)
+    rp, col, _ = W.from_coo(n, rows, cols)
+    col = col.astype(np.int32)
+    t_rp, t_col = _to(cuda_dev, rp, col)
+    for convert, bits in ((D.damn_csr_to_dacsr, 16), (D.damn_csr_to_dacsr_noalloc, 16)):
+        if convert is D.damn_csr_to_dacsr_noalloc:
+            out = torch.empty(len(col), dtype=torch.int16, device=cuda_dev)
+            _, info = convert(t_rp, t_col, n, out)
+        else:
+            _, info = convert(t_rp, t_col, n)
+        ref = OD.fit_check(n, n, rp, col, bits=bits)
+        assert ref.min_off == -2 ** 31 - 5 and ref.max_off == 2 ** 31 - 1 - 600
+        sat = lambda v: max(-2 ** 31, min(2 ** 31 - 1, v))
+        assert (info.min_off, info.max_off, info.n_fit, info.n_bad, info.fits) == \
+            (sat(ref.min_off), sat(ref.max_off), ref.n_fit, ref.n_bad, False)
+        assert info.w == 2 ** 31
+
+
 def test_laplace3d_full_size_and_scrambled(D, cuda_dev):
     m = 128
     rp, col, _ = W.laplace3d_7pt(m)

@@ -1,4 +1,4 @@
-"""DA-CSR-8 (int8 offsets; the int8 index width of Section 3, Fig. 3)
+"""DA-CSR-8 (int8 offsets; the int8 index width of Section 2, Fig. 3)
 through the C ABI: conversion and fit check bit-exact with the oracle, and
 SpMV bitwise equal to DA-CSR-16 and CSR-32 under one plan, bitwise equal to
 the oracle on dyadic inputs, within the error bound otherwise."""

@@ -267,3 +267,31 @@ def test_heuristic_ragged_rows(D, cuda_dev, h, expect):
     got = _run(D, m, x, plan=plan)
     _bound_check(m, x, got)
     assert np.array_equal(got, _run(D, m, x, plan=plan, fmt="csr"))
+
+
+def test_plan_rejects_other_arrays(D, cuda_dev):
+    """A plan's tiles and x windows belong to the arrays it was built from:
+    a call with another rowptr, or another index array of the plan's own
+    format, is refused before any device work (a different pattern would
+    read rows and x slots the plan never prepared); the CSR-32 copy of the
+    same matrix is accepted under a plan built from its DA-CSR-16 offsets."""
+    rng = np.random.default_rng(31)
+    n = 3000
+    rp, col, val = W.random_banded(n, 50, rng)
+    m = Mat(D, cuda_dev, n, n, rp, col, val)
+    plan = D.Plan(m.t_rp, len(col), n, torch.float64, idx=m.t_off)
+    x = _t(cuda_dev, W.uniform_vector(n, rng))
+    y = torch.zeros(n, dtype=torch.float64, device=cuda_dev)
+    other_rp = m.t_rp.clone()
+    other_off = m.t_off.clone()
+    f = D._lib.damn_spmv_dacsr16
+    rc = f(n, n, len(col), D._ptr(other_rp), D._ptr(m.t_off), D._ptr(m.t_val), D.DAMN_F64,
+           D._ptr(x), D._ptr(y), 1.0, 0.0, plan.handle, D._stream())
+    assert rc == D.DAMN_ERR_INVALID_ARG and "rowptr" in D.last_error()
+    rc = f(n, n, len(col), D._ptr(m.t_rp), D._ptr(other_off), D._ptr(m.t_val), D.DAMN_F64,
+           D._ptr(x), D._ptr(y), 1.0, 0.0, plan.handle, D._stream())
+    assert rc == D.DAMN_ERR_INVALID_ARG and "index array" in D.last_error()
+    # the CSR-32 copy of the same matrix under the DA-CSR-16 plan: accepted
+    D.damn_spmv_csr32(m.t_rp, m.t_col, m.t_val, x, y, plan=plan)
+    torch.cuda.synchronize()
+    assert D.damn_device_status() == 0

@@ -15,6 +15,7 @@ import pytest
 import torch
 
 import workloads as W
+from oracle import dacsr as OD
 
 pytestmark = pytest.mark.gpu
 
@@ -30,8 +31,14 @@ def _compare(D, dev, n_rows, n_cols, rp, col):
     got_off, got = D.damn_csr_to_dacsr_noalloc(t_rp, t_col, n_cols, off)
     torch.cuda.synchronize()
     assert got == ref
+    # and against the CPU oracle's fit check and translation
+    o = OD.fit_check(n_rows, n_cols, rp, col)
+    assert (got.min_off, got.max_off, got.w, got.n_fit, got.n_bad, bool(got.fits)) == \
+        (o.min_off, o.max_off, o.w, o.n_fit, o.n_bad, o.fits)
     if ref.fits:
         assert torch.equal(got_off, ref_off)
+        assert np.array_equal(got_off.cpu().numpy(),
+                              OD.translate(n_rows, rp, col).astype(np.int16))
     return got
 
 
