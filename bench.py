@@ -218,7 +218,23 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-PROFILE_CASES = ("stencil27_160_rows_long", "batch512_f64_k1")
+PROFILE_CASES = ("stencil27_160_rows_long", "batch512_f64_k1", "laplace3d_128",
+                 "banded_<n>_h<h>_<tiling>_<fmt>")
+
+
+def profile_case(name):
+    """argparse type of --case: a fixed case name, or a random banded case
+    banded_<n>_h<h>_<tiling>_<fmt> (n like 1e6, tiling auto / rows /
+    rows_long / slices, fmt da16 / csr32)."""
+    if name in PROFILE_CASES[:3]:
+        return name
+    parts = name.split("_")
+    tiling = "_".join(parts[3:-1])
+    ok = (len(parts) >= 5 and parts[0] == "banded" and parts[2].startswith("h")
+          and (tiling == "auto" or tiling in TILING_NAMES) and parts[-1] in ("da16", "csr32"))
+    if not ok:
+        raise argparse.ArgumentTypeError(f"unknown case {name!r}; one of {PROFILE_CASES}")
+    return name
 
 
 def run_case(args):
@@ -236,7 +252,37 @@ def run_case(args):
     from paper_2307_06305_gb300 import damn as D
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
-    if args.case == "stencil27_160_rows_long":
+    if args.case.startswith("banded_"):
+        parts = args.case.split("_")
+        n, h, fmt = int(float(parts[1])), int(parts[2][1:]), parts[-1]
+        tiling = "_".join(parts[3:-1])
+        rp, col, val = W.random_banded(n, h, W.rng_for(3, 0))
+        nnz = len(col)
+        t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
+        off, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
+        t_val = torch.from_numpy(val).to(dev)
+        x = torch.from_numpy(W.uniform_vector(n, W.rng_for(3, 100))).to(dev)
+        y = torch.empty(n, dtype=torch.float64, device=dev)
+        plan = D.Plan(t_rp, nnz, n, torch.float64, idx=off)
+        if tiling != "auto":
+            plan.set_tiling(TILING_NAMES.index(tiling))
+        for _ in range(args.steps):
+            if fmt == "da16":
+                D.damn_spmv_dacsr16(t_rp, off, t_val, x, y, plan=plan)
+            else:
+                D.damn_spmv_csr32(t_rp, t_col, t_val, x, y, plan=plan)
+    elif args.case == "laplace3d_128":
+        rp, col, val, xh = build_inputs()
+        n, nnz = len(rp) - 1, len(col)
+        t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
+        off, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
+        t_val = torch.from_numpy(val).to(dev)
+        x = torch.from_numpy(xh).to(dev)
+        y = torch.empty(n, dtype=torch.float64, device=dev)
+        plan = D.Plan(t_rp, nnz, n, torch.float64, idx=off)
+        for _ in range(args.steps):
+            D.damn_spmv_dacsr16(t_rp, off, t_val, x, y, plan=plan)
+    elif args.case == "stencil27_160_rows_long":
         rp, col, val = W.stencil27(160)
         n, nnz = len(rp) - 1, len(col)
         t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
@@ -608,7 +654,9 @@ BANDED_POINTS = ((100_000, 100), (100_000, 1000), (100_000, 30000),
 BANDED_POINTS_FULL = tuple((n, h) for n in (100_000, 300_000, 1_000_000, 3_000_000, 10_000_000,
                                             20_000_000) for h in (100, 1000, 30000))
 L2_BYTES = 126e6
-TILING_NAMES = ("slices", "rows", "rows_long")   # DAMN_TILING_* 0, 1, 2
+TILING_NAMES = ("slices", "rows", "rows_long", "band", "lanes4", "lanes8", "lanes16",
+                "lanes32")   # DAMN_TILING_* 0 .. 7
+BANDED_TILINGS = (0, 1, 2, 3, 4)  # the tilings timed in the banded section
 
 
 def section_banded(D, torch, dev, reps, full=False):
@@ -641,7 +689,8 @@ def section_banded(D, torch, dev, reps, full=False):
               "heuristic_tiling": TILING_NAMES[desc["tiling"]],
               "row_efficiency": round(desc["row_efficiency"], 3), "max_row": desc["max_row"],
               "tilings": {}}
-        for tiling, tname in enumerate(TILING_NAMES):
+        for tiling in BANDED_TILINGS:
+            tname = TILING_NAMES[tiling]
             for pl in plans:
                 pl.set_tiling(tiling)
             tt = {"x_staged_tiles_frac": round(plans[0].describe()["x_staged_tiles"]
@@ -720,7 +769,7 @@ def main():
                     help="parts (streams) each end-to-end upload / download is split into")
     ap.add_argument("--tiling", default="auto", choices=["auto", "rows", "rows_long", "slices"],
                     help="headline plan tiling: autotuned, or fixed")
-    ap.add_argument("--case", default=None, choices=PROFILE_CASES,
+    ap.add_argument("--case", default=None, type=profile_case,
                     help="run only the launches of one profiled kernel (for ncu), no timing")
     args = ap.parse_args()
 

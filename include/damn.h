@@ -221,46 +221,75 @@ typedef struct {
   int32_t max_row;       /* longest row                                        */
   int32_t dtype;
   int32_t tiling;        /* DAMN_TILING_*                                      */
-  int32_t x_staged_tiles;/* tiles whose x window is staged in shared memory    */
+  int32_t x_staged_tiles;/* tiles whose x window is staged in shared memory
+                           (x windows of <= 4 segments; 0 for DAMN_TILING_BAND,
+                           whose ring is filled as the kernel runs)           */
+  int32_t stages_requested; /* ring depth set by damn_plan_set_stages or the
+                           autotuner (0: automatic)                           */
 } damn_plan_desc;
 
 /* Tilings (see damn_plan_set_tiling). */
-#define DAMN_TILING_SLICES    0
-#define DAMN_TILING_ROWS      1
-#define DAMN_TILING_ROWS_LONG 2
+#define DAMN_TILING_SLICES        0
+#define DAMN_TILING_ROWS          1
+#define DAMN_TILING_ROWS_LONG     2
+#define DAMN_TILING_BAND          3
+#define DAMN_TILING_ROWS_LANES4   4
+#define DAMN_TILING_ROWS_LANES8   5
+#define DAMN_TILING_ROWS_LANES16  6
+#define DAMN_TILING_ROWS_LANES32  7
 
 /* Builds a plan for one matrix and value dtype: the partition of the rows
- * into tiles, the compute mode (chosen from the row-length statistics:
- * DAMN_TILING_ROWS or _ROWS_LONG when rows are uniform inside 32-row groups;
- * _ROWS_LONG also for ragged rows (row_efficiency >= 0.3) when its tiles fit
- * a stage and at least 90 % of their x windows are staged;
- * DAMN_TILING_SLICES otherwise) and, when idx (col for DAMN_FMT_CSR32, off
- * for DAMN_FMT_DACSR16 / DAMN_FMT_DACSR8) is given, the x window of every
- * tile: the tile's sorted distinct columns cut into at most 4 contiguous
- * segments (gaps of up to 32 columns merged), staged in shared memory by the SpMV kernels so that
- * x is not gathered from global memory (the band-window staging of DA-CSR).
- * Tiles whose window does not fit gather x from global memory.  idx may be
- * NULL (no x windows).  Reads rowptr/idx on the device; synchronises.
- * rowptr and idx must stay valid while the plan is used.  The plan owns device
- * memory until damn_plan_destroy.  One plan serves the CSR-32, DA-CSR-16 and
- * DA-CSR-8 copies of the same matrix, giving bitwise equal results. */
+ * into tiles and the compute mode (the tiling), chosen from the row-length
+ * statistics: rows of uniform length inside 32-row groups (row_efficiency
+ * >= 0.85) get a rows tiling with the fewest lanes per row (1, 2, 4, 8, 16
+ * or 32) that keeps a row's entries in registers and a tile in a stage;
+ * ragged rows get DAMN_TILING_BAND.  When idx (col for DAMN_FMT_CSR32, off
+ * for DAMN_FMT_DACSR16 / DAMN_FMT_DACSR8) is given, the plan also prepares
+ * how the SpMV kernels stage x in shared memory (the band-window staging of
+ * DA-CSR: row r reads x only in [r - w, r + w], Eq. (2)): for rows and
+ * slices tilings the x window of every tile -- its sorted distinct columns
+ * cut into at most 4 contiguous segments (gaps of up to 32 columns merged);
+ * for the band tiling the column range of every tile.  Tiles whose x cannot
+ * be staged gather it from global memory.  idx may be NULL (no staging).
+ * Reads rowptr/idx on the device; synchronises.  rowptr and idx must stay
+ * valid while the plan is used, and an SpMV given this plan must pass these
+ * same rowptr and (for the plan's own format) idx arrays; another index
+ * format's copy of the same matrix is accepted.  The plan owns device
+ * memory until damn_plan_destroy.  One plan serves the CSR-32, DA-CSR-16
+ * and DA-CSR-8 copies of the same matrix, giving bitwise equal results. */
 int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
                      int format, const void *idx, int dtype, void *stream, damn_plan **out);
 
-/* Times the three tilings on the given operands (format DAMN_FMT_*; idx is
- * col or off) and keeps the fastest in the plan.  y is overwritten.
- * Synchronises stream. */
+/* Autotuner: times every tiling on the given operands (format DAMN_FMT_*;
+ * idx is col or off) -- rows with 1 and 2 lanes per row, balanced slices,
+ * band, and rows with 4 / 8 / 16 / 32 lanes per row where an average row has
+ * at least two entries per lane -- keeps the fastest, then times ring depths
+ * of 2 to 6 stages for it and keeps one only when it is at least 3 % faster
+ * than the automatic depth.  y is overwritten.  Synchronises stream. */
 int damn_plan_autotune(damn_plan *plan, int format, const void *idx, const void *val,
                        const void *x, void *y, void *stream);
 
-/* Pins the plan's tiling: DAMN_TILING_SLICES (tiles balanced on rows +
- * entries, each computed as balanced entry slices), DAMN_TILING_ROWS (tiles
- * of 256 rows with FP64 values, one row per thread, or 512 rows with FP32 /
- * BF16 values, two rows per thread; short rows), DAMN_TILING_ROWS_LONG
- * (128-row tiles with larger stages, two lanes per row whose partial sums
- * are added at the end; rows of a few dozen).
- * Recomputes the x windows; synchronises the legacy default stream. */
+/* Pins the plan's tiling:
+ *  DAMN_TILING_ROWS: tiles of 256 rows with FP64 values, one row per
+ *    thread, or 512 rows with FP32 / BF16 values, two rows per thread;
+ *  DAMN_TILING_ROWS_LONG: 128-row tiles, two lanes per row;
+ *  DAMN_TILING_ROWS_LANES4 / 8 / 16 / 32: tiles of 64 / 32 / 16 / 8 rows,
+ *    4 / 8 / 16 / 32 lanes per row (lane i takes entries i, i + E, ...; the
+ *    lanes' partial sums are added by a butterfly);
+ *  DAMN_TILING_SLICES: tiles balanced on rows + entries, each thread one
+ *    contiguous slice of entries, x windows of up to 4 segments;
+ *  DAMN_TILING_BAND: the same balanced tiles and slices, each CTA walking a
+ *    contiguous run of tiles with x in a shared-memory ring (column c in slot
+ *    c mod W, W = 8192 for FP64 x, 16384 for FP32 x); a tile whose columns
+ *    the ring cannot hold reads x from global memory.
+ * Recomputes the staging data; synchronises the legacy default stream. */
 int damn_plan_set_tiling(damn_plan *plan, int tiling);
+
+/* Ring depth (shared-memory stages per CTA) of the plan's SpMV launches:
+ * 0 = automatic (the deepest ring that keeps the kernel's CTAs per SM), or
+ * 2 .. 8; a depth that does not fit the kernel's shared memory falls back to
+ * automatic.  No device work. */
+int damn_plan_set_stages(damn_plan *plan, int32_t stages);
 
 int damn_plan_describe(const damn_plan *plan, damn_plan_desc *h_desc);
 int damn_plan_destroy(damn_plan *plan);

@@ -15,6 +15,7 @@
 #include <mutex>
 
 #include "damn_common.cuh"
+#include "spmv_band.cuh"
 #include "spmv_internal.h"
 #include "spmv_kernel.cuh"
 
@@ -23,102 +24,50 @@ using namespace damn::spmvk;
 namespace damn {
 namespace {
 
-constexpr int kMaxDev = 64;
 constexpr int kRowWeight = 4;       // merge-path weight of a row against an entry
 constexpr int kBalancedItems = 2048;
 constexpr int kXGap = 32;           // columns: smaller gaps are staged, not split
-// every tile's row pointers must fit a stage
-// ragged rows run two lanes per row (rows-long tiling) when the row
-// efficiency is at least this and at least this fraction of the tiles have a
-// staged x window
-constexpr double kRaggedLongMinEff = 0.3;
-constexpr double kRaggedLongMinStaged = 0.9;
 static_assert(kBalancedItems / kRowWeight <= CfgSlices::CAP_ROWS, "balanced tiles too tall");
 static_assert(CfgShort::TILE_ROWS <= CfgShort::CAP_ROWS &&
                   CfgShortNarrow::TILE_ROWS <= CfgShortNarrow::CAP_ROWS &&
                   CfgLong::TILE_ROWS <= CfgLong::CAP_ROWS && 256 <= CfgSlices::CAP_ROWS,
               "row tiles too tall");
+static_assert(kBalancedItems <= CfgBand64::CAP_NZ && kBalancedItems / kRowWeight <= CfgBand64::CAP_ROWS &&
+                  kBalancedItems <= CfgBand32::CAP_NZ &&
+                  kBalancedItems / kRowWeight <= CfgBand32::CAP_ROWS,
+              "balanced tiles exceed a band stage");
 
 // ----------------------------------------------------------------------------
-// Launch
+// Launch: one launcher per (index format, value type), in spmv_inst_*.cu
 // ----------------------------------------------------------------------------
-template <bool PLAIN, typename V, typename I, class C, int NS>
-int launch_kernel(SpmvParams p, cudaStream_t s, int *gs_out) {
-  using L = Layout<V, I, C>;
-  // per device and mode: chosen ring depth and CTAs per SM (0 = not yet known)
-  static int stages_of[kMaxDev][2], occ_of[kMaxDev][2];
-  static std::mutex mu;
-  int dev = 0;
-  DAMN_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDev) return set_error(DAMN_ERR_UNSUPPORTED, "device index too large");
-  const int mode = p.mode == 1 ? 1 : 0;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (!occ_of[dev][mode]) {
-      int max_optin = 0;
-      DAMN_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-      DAMN_CUDA(cudaFuncSetAttribute(k_spmv<PLAIN, V, I, C, NS>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin));
-      // deepest ring that keeps C::MINB CTAs per SM (at least two stages)
-      int best_s = 2, best_o = 0;
-      for (int st = kMaxStages; st >= 2; --st) {
-        if (L::total(st, mode) > (size_t)max_optin) continue;
-        int o = 0;
-        DAMN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_spmv<PLAIN, V, I, C, NS>,
-                                                                C::NT + 32, L::total(st, mode)));
-        if (o >= C::MINB) { best_s = st; best_o = o; break; }
-        if (o > best_o) { best_s = st; best_o = o; }
-      }
-      stages_of[dev][mode] = best_s;
-      occ_of[dev][mode] = std::max(1, best_o);
-    }
-  }
-  p.stages = stages_of[dev][mode];
-  const int grid = std::max(1, std::min(p.ntiles, occ_of[dev][mode] * sm_count()));
-  if (gs_out) { gs_out[0] = grid; gs_out[1] = p.stages; }
-  if (p.ntiles == 0) return DAMN_OK;
-  k_spmv<PLAIN, V, I, C, NS><<<grid, C::NT + 32, L::total(p.stages, mode), s>>>(p);
-  DAMN_CHECK_LAUNCH("k_spmv");
-  return DAMN_OK;
-}
-
-template <typename V, typename I, class C>
-int launch_cfg(const SpmvParams &p, cudaStream_t s, int *gs) {
-  const bool plain = p.ab_mode == 0 && !p.dot_w && !p.dot_self && !p.dot_partials;
-  // rows mode with every x window of at most 3 segments: one compare fewer
-  // per entry in the column -> slot map
-  if (p.mode == 0 && p.max_nseg <= 3) {
-    if (plain) return launch_kernel<true, V, I, C, 3>(p, s, gs);
-    return launch_kernel<false, V, I, C, 3>(p, s, gs);
-  }
-  if (plain) return launch_kernel<true, V, I, C, kXSegMax>(p, s, gs);
-  return launch_kernel<false, V, I, C, kXSegMax>(p, s, gs);
-}
-
-template <typename V, typename I>
-int launch_types(const SpmvParams &p, int shape, cudaStream_t s, int *gs) {
-  if (shape == 1) return launch_cfg<V, I, CfgLong>(p, s, gs);
-  if (shape == 2) return launch_cfg<V, I, CfgSlices>(p, s, gs);
-  if constexpr (sizeof(V) < 8)
-    return launch_cfg<V, I, CfgShortNarrow>(p, s, gs);
-  else
-    return launch_cfg<V, I, CfgShort>(p, s, gs);
-}
+}  // namespace
+#define DAMN_DECL_LAUNCH(NAME) int NAME(const SpmvParams &, int, cudaStream_t, int *);
+DAMN_DECL_LAUNCH(spmv_launch_csr32_f64)
+DAMN_DECL_LAUNCH(spmv_launch_csr32_f32)
+DAMN_DECL_LAUNCH(spmv_launch_csr32_bf16)
+DAMN_DECL_LAUNCH(spmv_launch_dacsr16_f64)
+DAMN_DECL_LAUNCH(spmv_launch_dacsr16_f32)
+DAMN_DECL_LAUNCH(spmv_launch_dacsr16_bf16)
+DAMN_DECL_LAUNCH(spmv_launch_dacsr8_f64)
+DAMN_DECL_LAUNCH(spmv_launch_dacsr8_f32)
+DAMN_DECL_LAUNCH(spmv_launch_dacsr8_bf16)
+#undef DAMN_DECL_LAUNCH
+namespace {
 
 int launch_any(const SpmvParams &p, int dtype, int fmt, int shape, cudaStream_t s, int *gs) {
   if (fmt == DAMN_FMT_DACSR16) {
-    if (dtype == DAMN_F64) return launch_types<double, int16_t>(p, shape, s, gs);
-    if (dtype == DAMN_F32) return launch_types<float, int16_t>(p, shape, s, gs);
-    return launch_types<__nv_bfloat16, int16_t>(p, shape, s, gs);
+    if (dtype == DAMN_F64) return spmv_launch_dacsr16_f64(p, shape, s, gs);
+    if (dtype == DAMN_F32) return spmv_launch_dacsr16_f32(p, shape, s, gs);
+    return spmv_launch_dacsr16_bf16(p, shape, s, gs);
   }
   if (fmt == DAMN_FMT_DACSR8) {
-    if (dtype == DAMN_F64) return launch_types<double, int8_t>(p, shape, s, gs);
-    if (dtype == DAMN_F32) return launch_types<float, int8_t>(p, shape, s, gs);
-    return launch_types<__nv_bfloat16, int8_t>(p, shape, s, gs);
+    if (dtype == DAMN_F64) return spmv_launch_dacsr8_f64(p, shape, s, gs);
+    if (dtype == DAMN_F32) return spmv_launch_dacsr8_f32(p, shape, s, gs);
+    return spmv_launch_dacsr8_bf16(p, shape, s, gs);
   }
-  if (dtype == DAMN_F64) return launch_types<double, int32_t>(p, shape, s, gs);
-  if (dtype == DAMN_F32) return launch_types<float, int32_t>(p, shape, s, gs);
-  return launch_types<__nv_bfloat16, int32_t>(p, shape, s, gs);
+  if (dtype == DAMN_F64) return spmv_launch_csr32_f64(p, shape, s, gs);
+  if (dtype == DAMN_F32) return spmv_launch_csr32_f32(p, shape, s, gs);
+  return spmv_launch_csr32_bf16(p, shape, s, gs);
 }
 
 // ----------------------------------------------------------------------------
@@ -323,6 +272,48 @@ __global__ void k_count_staged(const XSeg *xs, int ntiles, int *count) {
   }
 }
 
+// {min, max} column of the entries of every balanced tile (one block per
+// tile, a thread per row); {INT_MAX, INT_MIN} for a tile without entries.
+__global__ void __launch_bounds__(256)
+k_plan_colrange(const int *__restrict__ rowptr, const void *idx, int fmt, int ntiles,
+                const int2 *__restrict__ bounds, int2 *out) {
+  __shared__ int s_lo[8], s_hi[8];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int2 b0 = bounds[t], b1 = bounds[t + 1];
+    int lo = INT_MAX, hi = INT_MIN;
+    for (int r = b0.x + threadIdx.x; r < b1.x; r += blockDim.x) {
+      for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+        int c;
+        if (fmt == DAMN_FMT_CSR32) c = static_cast<const int *>(idx)[k];
+        else if (fmt == DAMN_FMT_DACSR8) c = r + static_cast<const int8_t *>(idx)[k];
+        else c = r + static_cast<const int16_t *>(idx)[k];
+        lo = min(lo, c);
+        hi = max(hi, c);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) { s_lo[threadIdx.x >> 5] = lo; s_hi[threadIdx.x >> 5] = hi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { lo = min(lo, s_lo[w]); hi = max(hi, s_hi[w]); }
+      out[t] = make_int2(lo, hi);
+    }
+    __syncthreads();
+  }
+}
+
+// Most entries of any tile of tile_rows consecutive rows (*out, atomicMax).
+__global__ void k_plan_max_tile(int nrows, const int *__restrict__ rowptr, int tile_rows, int *out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long r0 = t * tile_rows;
+  if (r0 >= nrows) return;
+  const int r1 = (int)min((long long)nrows, r0 + tile_rows);
+  atomicMax(out, rowptr[r1] - rowptr[r0]);
+}
+
 }  // namespace
 }  // namespace damn
 
@@ -333,8 +324,8 @@ struct damn_plan {
   const int32_t *rowptr;  // caller's arrays (kept for the autotuner and the x windows)
   const void *idx;        // column indices (may be NULL: no x windows)
   int fmt;
-  int mode;               // 0 rows per thread, 1 balanced slices
-  int shape;              // kernel configuration: 0 CfgShort, 1 CfgLong, 2 CfgSlices
+  int mode;               // 0 rows, 1 balanced slices, 2 band
+  int shape;              // kernel configuration (spmvk::Shape)
   int rows_per_tile;      // > 0 fixed row tiles, 0 bounds
   int ntiles;
   int2 *d_bounds;         // bounds of the current tiling (NULL for fixed rows)
@@ -342,11 +333,13 @@ struct damn_plan {
   int ntiles_balanced;
   XSeg *d_xseg;           // x windows of the current tiling (NULL: none)
   int xseg_cap;
+  int2 *d_colrange;       // band mode: column range of every balanced tile (NULL: none)
   int staged_tiles;
   int max_nseg;           // most x segments of a tile's window (rows mode kernel variant)
   int max_row;
   double row_eff;
   int max_tile_short, max_tile_long;
+  int stages_req;         // requested ring depth (0: automatic)
   int grid, stages;       // geometry of the last launch
 };
 
@@ -357,14 +350,51 @@ int spmv_max_grid() { return 8 * sm_count(); }
 // Tile height, stage entry capacity and staged-x capacity of the kernel
 // configuration a plan shape uses for a value type (must match launch_types).
 struct CfgGeom {
-  int tile_rows, cap_nz, xcap;
+  int tile_rows, cap_nz, xcap, threads;
 };
 static CfgGeom cfg_geom(int shape, int dtype) {
-  if (shape == 1) return {CfgLong::TILE_ROWS, CfgLong::CAP_NZ, CfgLong::XCAP};
-  if (shape == 2) return {0, CfgSlices::CAP_NZ, CfgSlices::XCAP};
+  switch (shape) {
+    case kShapeLong: return {CfgLong::TILE_ROWS, CfgLong::CAP_NZ, CfgLong::XCAP, CfgLong::NT};
+    case kShapeSlices: return {0, CfgSlices::CAP_NZ, CfgSlices::XCAP, CfgSlices::NT};
+    case kShapeBand:
+      return {0, CfgBand64::CAP_NZ, dtype == DAMN_F64 ? CfgBand64::W : CfgBand32::W,
+              CfgBand64::G * CfgBand64::NT};
+    case kShapeLanes4: return {CfgLanes4::TILE_ROWS, CfgLanes4::CAP_NZ, CfgLanes4::XCAP, 256};
+    case kShapeLanes8: return {CfgLanes8::TILE_ROWS, CfgLanes8::CAP_NZ, CfgLanes8::XCAP, 256};
+    case kShapeLanes16: return {CfgLanes16::TILE_ROWS, CfgLanes16::CAP_NZ, CfgLanes16::XCAP, 256};
+    case kShapeLanes32: return {CfgLanes32::TILE_ROWS, CfgLanes32::CAP_NZ, CfgLanes32::XCAP, 256};
+    default: break;
+  }
   if (dtype != DAMN_F64)
-    return {CfgShortNarrow::TILE_ROWS, CfgShortNarrow::CAP_NZ, CfgShortNarrow::XCAP};
-  return {CfgShort::TILE_ROWS, CfgShort::CAP_NZ, CfgShort::XCAP};
+    return {CfgShortNarrow::TILE_ROWS, CfgShortNarrow::CAP_NZ, CfgShortNarrow::XCAP, 256};
+  return {CfgShort::TILE_ROWS, CfgShort::CAP_NZ, CfgShort::XCAP, 256};
+}
+
+// Public tiling <-> kernel shape.
+static int shape_of_tiling(int tiling) {
+  switch (tiling) {
+    case DAMN_TILING_SLICES: return kShapeSlices;
+    case DAMN_TILING_ROWS: return kShapeShort;
+    case DAMN_TILING_ROWS_LONG: return kShapeLong;
+    case DAMN_TILING_BAND: return kShapeBand;
+    case DAMN_TILING_ROWS_LANES4: return kShapeLanes4;
+    case DAMN_TILING_ROWS_LANES8: return kShapeLanes8;
+    case DAMN_TILING_ROWS_LANES16: return kShapeLanes16;
+    case DAMN_TILING_ROWS_LANES32: return kShapeLanes32;
+    default: return -1;
+  }
+}
+static int tiling_of_shape(int shape) {
+  switch (shape) {
+    case kShapeSlices: return DAMN_TILING_SLICES;
+    case kShapeLong: return DAMN_TILING_ROWS_LONG;
+    case kShapeBand: return DAMN_TILING_BAND;
+    case kShapeLanes4: return DAMN_TILING_ROWS_LANES4;
+    case kShapeLanes8: return DAMN_TILING_ROWS_LANES8;
+    case kShapeLanes16: return DAMN_TILING_ROWS_LANES16;
+    case kShapeLanes32: return DAMN_TILING_ROWS_LANES32;
+    default: return DAMN_TILING_ROWS;
+  }
 }
 
 static int make_params(const SpmvCall &c, const damn_plan *plan, SpmvParams &p, int &shape) {
@@ -392,8 +422,10 @@ static int make_params(const SpmvCall &c, const damn_plan *plan, SpmvParams &p, 
     p.rows_per_tile = plan->rows_per_tile;
     p.ntiles = plan->ntiles;
     p.bounds = plan->d_bounds;
-    p.xseg = plan->d_xseg;
-    p.max_nseg = plan->d_xseg ? plan->max_nseg : kXSegMax;
+    p.xseg = plan->mode == 2 ? nullptr : plan->d_xseg;
+    p.colrange = plan->mode == 2 ? plan->d_colrange : nullptr;
+    p.stages_req = plan->stages_req;
+    p.max_nseg = p.xseg ? plan->max_nseg : kXSegMax;
     shape = plan->shape;
   } else {
     p.mode = 1;
@@ -454,6 +486,8 @@ static int check_spmv_args(const char *fn, int fmt, int32_t nrows, int32_t ncols
     return set_error(DAMN_ERR_INVALID_ARG, "%s: bad dtype %d", fn, dtype);
   if (nrows > 0 && (!rowptr || !y)) return set_error(DAMN_ERR_INVALID_ARG, "%s: NULL pointer", fn);
   if (nnz > 0 && (!idx || !val || !x)) return set_error(DAMN_ERR_INVALID_ARG, "%s: NULL pointer", fn);
+  if (nnz > 0 && ncols == 0)
+    return set_error(DAMN_ERR_INVALID_ARG, "%s: entries but no columns (ncols == 0)", fn);
   if (!aligned16(rowptr) || !aligned16(idx) || !aligned16(val) || !aligned16(x) || !aligned16(y))
     return set_error(DAMN_ERR_INVALID_ARG, "%s: pointers must be 16-byte aligned", fn);
   return plan_check(fn, plan, fmt, nrows, ncols, nnz, rowptr, idx, dtype);
@@ -502,12 +536,13 @@ extern "C" int damn_spmv_dacsr8(int32_t nrows, int32_t ncols, int64_t nnz, const
 static void plan_free_device(damn_plan *pl) {
   if (pl->d_bounds_balanced) cudaFree(pl->d_bounds_balanced);
   if (pl->d_xseg) cudaFree(pl->d_xseg);
+  if (pl->d_colrange) cudaFree(pl->d_colrange);
   pl->d_bounds_balanced = nullptr;
   pl->d_xseg = nullptr;
+  pl->d_colrange = nullptr;
   pl->d_bounds = nullptr;
 }
 
-// Recomputes the x windows for the plan's current tiling (synchronises).
 static int plan_xwindows(damn_plan *pl, cudaStream_t s) {
   pl->staged_tiles = 0;
   pl->max_nseg = kXSegMax;
@@ -542,27 +577,80 @@ static int plan_xwindows(damn_plan *pl, cudaStream_t s) {
   return DAMN_OK;
 }
 
+// Column range of every balanced tile, for band mode (once per plan).
+static int plan_colrange(damn_plan *pl, cudaStream_t s) {
+  if (pl->d_colrange || !pl->idx || pl->ntiles_balanced == 0) return DAMN_OK;
+  DAMN_CUDA(cudaMalloc(&pl->d_colrange, sizeof(int2) * (size_t)pl->ntiles_balanced));
+  const int blocks = std::min(pl->ntiles_balanced, 16 * sm_count());
+  k_plan_colrange<<<blocks, 256, 0, s>>>(pl->rowptr, pl->idx, pl->fmt, pl->ntiles_balanced,
+                                         pl->d_bounds_balanced, pl->d_colrange);
+  DAMN_CHECK_LAUNCH("k_plan_colrange");
+  DAMN_CUDA(cudaStreamSynchronize(s));
+  return DAMN_OK;
+}
+
 static int plan_use(damn_plan *pl, int tiling, cudaStream_t s) {
-  if (tiling == DAMN_TILING_SLICES) {
-    pl->mode = 1;
-    pl->shape = 2;
+  const int shape = shape_of_tiling(tiling);
+  pl->shape = shape;
+  if (shape == kShapeSlices || shape == kShapeBand) {
+    pl->mode = shape == kShapeBand ? 2 : 1;
     pl->rows_per_tile = 0;
     pl->ntiles = pl->ntiles_balanced;
     pl->d_bounds = pl->d_bounds_balanced;
   } else {
-    const int shape = tiling == DAMN_TILING_ROWS_LONG ? 1 : 0;
     pl->mode = 0;
-    pl->shape = shape;
     pl->rows_per_tile = cfg_geom(shape, pl->dtype).tile_rows;
     pl->ntiles = (pl->nrows + pl->rows_per_tile - 1) / pl->rows_per_tile;
     pl->d_bounds = nullptr;
   }
+  if (shape == kShapeBand) {
+    pl->staged_tiles = 0;
+    pl->max_nseg = kXSegMax;
+    return plan_colrange(pl, s);
+  }
   return plan_xwindows(pl, s);
 }
 
-static int plan_tiling_of(const damn_plan *pl) {
-  if (pl->mode == 1) return DAMN_TILING_SLICES;
-  return pl->shape == 1 ? DAMN_TILING_ROWS_LONG : DAMN_TILING_ROWS;
+static int plan_tiling_of(const damn_plan *pl) { return tiling_of_shape(pl->shape); }
+
+// Most entries of a tile of tile_rows consecutive rows (synchronises).
+static int plan_max_tile(const damn_plan *pl, int tile_rows, cudaStream_t s, int *out) {
+  *out = 0;
+  if (pl->nrows == 0) return DAMN_OK;
+  int *d = nullptr;
+  DAMN_CUDA(cudaMallocAsync(&d, sizeof(int), s));
+  DAMN_CUDA(cudaMemsetAsync(d, 0, sizeof(int), s));
+  const long long nt = (pl->nrows + (long long)tile_rows - 1) / tile_rows;
+  k_plan_max_tile<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(pl->nrows, pl->rowptr, tile_rows, d);
+  DAMN_CHECK_LAUNCH("k_plan_max_tile");
+  DAMN_CUDA(cudaMemcpyAsync(out, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DAMN_CUDA(cudaFreeAsync(d, s));
+  DAMN_CUDA(cudaStreamSynchronize(s));
+  return DAMN_OK;
+}
+
+// Rows-mode tiling for uniform rows of mean length `mean`: the fewest lanes
+// per row that keep at most 7 (one lane) or 14 (more lanes) of a row's
+// entries per lane, among the tilings whose tiles fit a stage.
+static int uniform_rows_tiling(const damn_plan *pl, double mean, cudaStream_t s, int *tiling) {
+  *tiling = -1;
+  const int cands[6] = {DAMN_TILING_ROWS, DAMN_TILING_ROWS_LONG, DAMN_TILING_ROWS_LANES4,
+                        DAMN_TILING_ROWS_LANES8, DAMN_TILING_ROWS_LANES16, DAMN_TILING_ROWS_LANES32};
+  const int lanes[6] = {1, 2, 4, 8, 16, 32};
+  for (int i = 0; i < 6; ++i) {
+    const CfgGeom g = cfg_geom(shape_of_tiling(cands[i]), pl->dtype);
+    const double per_lane = mean / lanes[i];
+    if (i < 5 && per_lane > (i == 0 ? 7.0 : 14.0)) continue;
+    int mt = 0;
+    if (i == 0) mt = pl->max_tile_short;
+    else if (i == 1) mt = pl->max_tile_long;
+    else {
+      int rc = plan_max_tile(pl, g.tile_rows, s, &mt);
+      if (rc) return rc;
+    }
+    if (mt <= g.cap_nz) { *tiling = cands[i]; return DAMN_OK; }
+  }
+  return DAMN_OK;
 }
 
 extern "C" int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
@@ -609,29 +697,19 @@ extern "C" int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const
   pl->max_tile_short = h.max_tile_short;
   pl->max_tile_long = h.max_tile_long;
   pl->row_eff = h.sum_group_max ? (double)nnz / (32.0 * (double)h.sum_group_max) : 1.0;
-  // Heuristic choice: one row per thread when rows are uniform inside 32-row
-  // groups and a row block fits a stage.  Rows of moderately varying length
-  // (random banded matrices: lengths LogNormal around a dozen) still run
-  // faster two lanes per row than as balanced slices, as long as the 128-row
-  // tiles fit a stage and their x windows are staged (measured on GB300:
-  // 73 vs 109 us for 1e6 rows, h = 100); when most windows are not staged
-  // (wide bands) the slices are faster.  Balanced slices otherwise.
-  int tiling = DAMN_TILING_SLICES;
-  const bool long_fits = pl->max_tile_long <= cfg_geom(1, dtype).cap_nz;
-  if (pl->row_eff >= 0.85 && pl->max_tile_short <= cfg_geom(0, dtype).cap_nz)
-    tiling = DAMN_TILING_ROWS;
-  else if (pl->row_eff >= 0.85 && long_fits)
-    tiling = DAMN_TILING_ROWS_LONG;
-  else if (pl->row_eff >= kRaggedLongMinEff && long_fits && pl->idx)
-    tiling = -1;  // decided by the staged x windows below
-  int rc;
-  if (tiling == -1) {
-    rc = plan_use(pl, DAMN_TILING_ROWS_LONG, s);
-    if (!rc && (double)pl->staged_tiles < kRaggedLongMinStaged * (double)pl->ntiles)
-      rc = plan_use(pl, DAMN_TILING_SLICES, s);
-  } else {
-    rc = plan_use(pl, tiling, s);
+  // Heuristic choice.  Rows of uniform length inside 32-row groups: rows
+  // mode with the fewest lanes per row that keep a row's entries in
+  // registers.  Ragged rows: band mode -- entry-balanced slices (a full warp
+  // of entries per FMA whatever the row lengths), x through the ring when
+  // the band is narrow enough and gathered otherwise.
+  int tiling = DAMN_TILING_BAND;
+  int rc = DAMN_OK;
+  if (pl->row_eff >= 0.85) {
+    int t = -1;
+    rc = uniform_rows_tiling(pl, nrows > 0 ? (double)nnz / nrows : 0.0, s, &t);
+    if (t >= 0) tiling = t;
   }
+  if (!rc) rc = plan_use(pl, tiling, s);
   if (rc) { plan_free_device(pl); delete pl; return rc; }
   *out = pl;
   return DAMN_OK;
@@ -653,36 +731,76 @@ extern "C" int damn_plan_autotune(damn_plan *plan, int format, const void *idx, 
   cudaEvent_t e0, e1;
   DAMN_CUDA(cudaEventCreate(&e0));
   DAMN_CUDA(cudaEventCreate(&e1));
-  const int cands[3] = {DAMN_TILING_ROWS, DAMN_TILING_ROWS_LONG, DAMN_TILING_SLICES};
-  float best_ms = 1e30f;
-  int best = plan_tiling_of(plan);
-  for (int ci = 0; ci < 3 && rc == DAMN_OK; ++ci) {
-    rc = plan_use(plan, cands[ci], s);
-    for (int w = 0; w < 2 && rc == DAMN_OK; ++w) rc = spmv_launch(c, plan, s, nullptr);
+  // best of 5 launches after 2 warm-up launches, in ms
+  auto time_plan = [&](float *out) {
+    int r2 = DAMN_OK;
+    for (int w = 0; w < 2 && r2 == DAMN_OK; ++w) r2 = spmv_launch(c, plan, s, nullptr);
     float tmin = 1e30f;
-    for (int r = 0; r < 5 && rc == DAMN_OK; ++r) {
+    for (int r = 0; r < 5 && r2 == DAMN_OK; ++r) {
       cudaEventRecord(e0, s);
-      rc = spmv_launch(c, plan, s, nullptr);
+      r2 = spmv_launch(c, plan, s, nullptr);
       cudaEventRecord(e1, s);
       cudaError_t ce = cudaEventSynchronize(e1);
-      if (ce != cudaSuccess) { rc = cuda_error(ce, "damn_plan_autotune"); break; }
+      if (ce != cudaSuccess) { r2 = cuda_error(ce, "damn_plan_autotune"); break; }
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       tmin = std::min(tmin, ms);
     }
-    if (tmin < best_ms) { best_ms = tmin; best = cands[ci]; }
+    *out = tmin;
+    return r2;
+  };
+  // 1. tilings: the fixed shapes, and the lanes-per-row tilings whose lanes
+  //    would each hold at least two entries of an average row
+  const double mean = (double)plan->nnz / plan->nrows;
+  int cands[8], nc = 0;
+  cands[nc++] = DAMN_TILING_ROWS;
+  cands[nc++] = DAMN_TILING_ROWS_LONG;
+  cands[nc++] = DAMN_TILING_SLICES;
+  cands[nc++] = DAMN_TILING_BAND;
+  const int lane_t[4] = {DAMN_TILING_ROWS_LANES4, DAMN_TILING_ROWS_LANES8, DAMN_TILING_ROWS_LANES16,
+                         DAMN_TILING_ROWS_LANES32};
+  for (int i = 0; i < 4; ++i)
+    if (mean >= 2.0 * (4 << i)) cands[nc++] = lane_t[i];
+  const int keep_stages = plan->stages_req;
+  plan->stages_req = 0;
+  float best_ms = 1e30f;
+  int best = plan_tiling_of(plan);
+  for (int ci = 0; ci < nc && rc == DAMN_OK; ++ci) {
+    rc = plan_use(plan, cands[ci], s);
+    float t = 1e30f;
+    if (!rc) rc = time_plan(&t);
+    if (t < best_ms) { best_ms = t; best = cands[ci]; }
   }
+  // 2. ring depth for the best tiling: automatic, or 2 .. 6 stages
+  int best_st = 0;
+  if (!rc) rc = plan_use(plan, best, s);
+  for (int st = 2; st <= 6 && rc == DAMN_OK; ++st) {
+    plan->stages_req = st;
+    float t = 1e30f;
+    rc = time_plan(&t);
+    if (plan->stages != st) continue;  // that depth does not fit this kernel
+    if (t < 0.97f * best_ms) { best_ms = t; best_st = st; }
+  }
+  plan->stages_req = rc ? keep_stages : best_st;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (rc) return rc;
-  return plan_use(plan, best, s);
+  return rc;
 }
 
 extern "C" int damn_plan_set_tiling(damn_plan *plan, int tiling) {
   if (!plan) return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_set_tiling: plan is NULL");
-  if (tiling != DAMN_TILING_SLICES && tiling != DAMN_TILING_ROWS && tiling != DAMN_TILING_ROWS_LONG)
+  if (shape_of_tiling(tiling) < 0)
     return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_set_tiling: bad tiling %d", tiling);
   return plan_use(plan, tiling, nullptr);
+}
+
+extern "C" int damn_plan_set_stages(damn_plan *plan, int32_t stages) {
+  if (!plan) return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_set_stages: plan is NULL");
+  if (stages != 0 && (stages < 2 || stages > kMaxStages))
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_set_stages: stages must be 0 or 2..%d",
+                     kMaxStages);
+  plan->stages_req = stages;
+  return DAMN_OK;
 }
 
 extern "C" int damn_plan_describe(const damn_plan *plan, damn_plan_desc *h_desc) {
@@ -692,12 +810,13 @@ extern "C" int damn_plan_describe(const damn_plan *plan, damn_plan_desc *h_desc)
   h_desc->ntiles = plan->ntiles;
   h_desc->grid = plan->grid;
   h_desc->stages = plan->stages;
-  h_desc->threads = plan->shape == 1 ? CfgLong::NT : plan->shape == 2 ? CfgSlices::NT : CfgShort::NT;
+  h_desc->threads = cfg_geom(plan->shape, plan->dtype).threads;
   h_desc->row_efficiency = plan->row_eff;
   h_desc->max_row = plan->max_row;
   h_desc->dtype = plan->dtype;
   h_desc->tiling = plan_tiling_of(plan);
   h_desc->x_staged_tiles = plan->staged_tiles;
+  h_desc->stages_requested = plan->stages_req;
   return DAMN_OK;
 }
 

@@ -1,0 +1,4 @@
+// SpMV kernels for dacsr8 indices and bf16 values (see spmv_launch.cuh).
+#include "spmv_launch.cuh"
+
+DAMN_SPMV_INSTANCE(spmv_launch_dacsr8_bf16, __nv_bfloat16, int8_t)

@@ -112,7 +112,9 @@ struct SpmvParams {
   int dot_self;
   double *dot_partials;
   int stages;          // depth of the shared-memory ring (<= kMaxStages)
+  int stages_req;      // requested depth (0: the deepest that keeps MINB CTAs per SM)
   int max_nseg;        // most x segments of any tile's window
+  const int2 *colrange;  // band mode: {min, max} column of every tile (NULL: none)
   int *status;
   unsigned long long timeout_ns;
 };
@@ -128,7 +130,8 @@ struct KCfg {
   static constexpr int MINB = MINB_, RPT = RPT_;
   static constexpr int E = E_;                       // lanes sharing one row (rows mode)
   static constexpr int TILE_ROWS = NT * RPT / E;
-  static_assert(E == 1 || E == 2 || E == 4, "1, 2 or 4 lanes per row");
+  static_assert(E == 1 || E == 2 || E == 4 || E == 8 || E == 16 || E == 32,
+                "a power of two from 1 to 32 lanes per row");
 };
 
 // Rows mode, short rows, FP64 values: 256 consumers (8 warps: two on each SM
@@ -148,10 +151,29 @@ struct KCfg {
 // rows of up to 28 entries stay in registers.
 // Slices mode: 256 consumers, two CTAs per SM, balanced tiles of up to 2048
 // entries and 512 rows.
+// Rows mode, E = 4, 8, 16, 32 lanes per row (rows of dozens to hundreds of
+// entries): the long-rows stages with tiles of 64, 32, 16 or 8 rows; each
+// lane keeps 14 of its row's entries in registers.
 using CfgShort = KCfg<256, 1792, 256, 1280, 3, 1>;
 using CfgShortNarrow = KCfg<256, 3584, 512, 2560, 3, 2>;
 using CfgLong = KCfg<256, 3584, 128, 1536, 2, 1, 2>;
 using CfgSlices = KCfg<256, 2048, 512, 1280, 2, 1>;
+using CfgLanes4 = KCfg<256, 3584, 64, 1536, 2, 1, 4>;
+using CfgLanes8 = KCfg<256, 3584, 32, 1536, 2, 1, 8>;
+using CfgLanes16 = KCfg<256, 3584, 16, 1536, 2, 1, 16>;
+using CfgLanes32 = KCfg<256, 3584, 8, 1536, 2, 1, 32>;
+
+// Plan shapes (kernel configurations); cfg_geom in spmv.cu gives their geometry.
+enum Shape {
+  kShapeShort = 0,   // rows, one lane per row (CfgShort / CfgShortNarrow)
+  kShapeLong = 1,    // rows, two lanes per row
+  kShapeSlices = 2,  // balanced tiles, entry slices, x windows of <= 4 segments
+  kShapeBand = 3,    // balanced tiles, entry slices, x ring (band mode)
+  kShapeLanes4 = 4,
+  kShapeLanes8 = 5,
+  kShapeLanes16 = 6,
+  kShapeLanes32 = 7,
+};
 
 constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -462,12 +484,20 @@ struct TileView {
   }
 };
 
+// x[c] read from global memory with c clamped into [0, ncols): a column
+// outside x (invalid input, e.g. offsets that did not fit their type) reads
+// a wrong entry of x instead of memory outside it.  One unsigned min.
+template <typename A>
+__device__ __forceinline__ A x_global(const A *xg, int c, int ncols) {
+  return ldg(xg + min(static_cast<unsigned>(c), static_cast<unsigned>(ncols - 1)));
+}
+
 // x value of column c of a tile starting at row r0: from the staged window or
 // gathered from global memory.
 template <typename A, class XM>
 __device__ __forceinline__ A x_at(const A *xg, const A *xs, const XM &xm, bool staged, int c,
-                                  int r0) {
-  return staged ? xs[xm.slot(c - r0)] : ldg(xg + c);
+                                  int r0, int ncols) {
+  return staged ? xs[xm.slot(c - r0)] : x_global(xg, c, ncols);
 }
 
 // Mode 0 -------------------------------------------------------------------
@@ -490,7 +520,8 @@ __device__ __noinline__ void rows_general(const SpmvParams &p, unsigned char *sm
     A acc = 0;
     for (int q = tv.rp[lr] - h.k0; q < tv.rp[lr + 1] - h.k0; ++q)
       acc = fma_acc(to_acc(tv.vs[q]),
-                    x_at(xg, tv.xs, xm, staged, static_cast<int>(tv.is[q]) + (DA ? row : 0), h.r0),
+                    x_at(xg, tv.xs, xm, staged, static_cast<int>(tv.is[q]) + (DA ? row : 0), h.r0,
+                         p.ncols),
                     acc);
     store_row<PLAIN>(p, row, acc, dsum);
   }
@@ -630,7 +661,7 @@ __device__ __forceinline__ void tile_slices(const SpmvParams &p, const TileHdr &
           while (tend <= q + u) { ++tcr; tend = rp[tcr + 1] - k0; }
           const int c = static_cast<int>(tv.is[q + u]) + (DA ? h.r0 + tcr : 0);
           av[u] = to_acc(tv.vs[q + u]);
-          xv[u] = x_at(xg, tv.xs, xm, staged, c, h.r0);
+          xv[u] = x_at(xg, tv.xs, xm, staged, c, h.r0, p.ncols);
         }
       }
 #pragma unroll

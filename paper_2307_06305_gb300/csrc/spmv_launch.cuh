@@ -1,0 +1,152 @@
+// Host-side launch of the SpMV kernels for one (value type, index type):
+// kernel configuration per plan shape, ring depth and grid size.  Included
+// by the instantiation units spmv_inst_*.cu, one per (index format, value
+// type), so that the many kernel variants compile in parallel.
+#pragma once
+
+#include <algorithm>
+#include <mutex>
+
+#include "damn_common.cuh"
+#include "spmv_band.cuh"
+#include "spmv_kernel.cuh"
+
+namespace damn {
+namespace spmvk {
+
+constexpr int kMaxDev = 64;
+
+// Occupancy of one kernel for every ring depth on one device, found once.
+struct Occ {
+  int known = 0;
+  int max_optin = 0;
+  int occ[kMaxStages + 1] = {};  // CTAs per SM at that depth (0: does not fit)
+};
+
+// Ring depth and CTAs per SM: the requested depth when it fits, else the
+// deepest ring that keeps `minb` CTAs per SM (at least two stages).
+template <class KFn, class TotalFn>
+int pick_geometry(KFn kernel, int threads, TotalFn total, int minb, int req, Occ (&cache)[kMaxDev],
+                  std::mutex &mu, int *stages, int *occ) {
+  int dev = 0;
+  DAMN_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) return set_error(DAMN_ERR_UNSUPPORTED, "device index too large");
+  std::lock_guard<std::mutex> lock(mu);
+  Occ &c = cache[dev];
+  if (!c.known) {
+    DAMN_CUDA(cudaDeviceGetAttribute(&c.max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    DAMN_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c.max_optin));
+    for (int st = 2; st <= kMaxStages; ++st) {
+      c.occ[st] = 0;
+      if (total(st) > (size_t)c.max_optin) continue;
+      int o = 0;
+      DAMN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, threads, total(st)));
+      c.occ[st] = o;
+    }
+    c.known = 1;
+  }
+  if (req >= 2 && req <= kMaxStages && c.occ[req] > 0) {
+    *stages = req;
+    *occ = c.occ[req];
+    return DAMN_OK;
+  }
+  int best_s = 2, best_o = 0;
+  for (int st = kMaxStages; st >= 2; --st) {
+    if (c.occ[st] >= minb) { best_s = st; best_o = c.occ[st]; break; }
+    if (c.occ[st] > best_o) { best_s = st; best_o = c.occ[st]; }
+  }
+  if (best_o == 0) return set_error(DAMN_ERR_UNSUPPORTED, "SpMV kernel does not fit this device");
+  *stages = best_s;
+  *occ = best_o;
+  return DAMN_OK;
+}
+
+template <bool PLAIN, typename V, typename I, class C, int NS>
+int launch_kernel(SpmvParams p, cudaStream_t s, int *gs_out) {
+  using L = Layout<V, I, C>;
+  static Occ cache[2][kMaxDev];
+  static std::mutex mu;
+  const int mode = p.mode == 1 ? 1 : 0;
+  int st = 2, occ = 1;
+  int rc = pick_geometry(k_spmv<PLAIN, V, I, C, NS>, C::NT + 32,
+                         [mode](int k) { return L::total(k, mode); }, C::MINB, p.stages_req,
+                         cache[mode], mu, &st, &occ);
+  if (rc) return rc;
+  p.stages = st;
+  const int grid = std::max(1, std::min(p.ntiles, occ * sm_count()));
+  if (gs_out) { gs_out[0] = grid; gs_out[1] = p.stages; }
+  if (p.ntiles == 0) return DAMN_OK;
+  k_spmv<PLAIN, V, I, C, NS><<<grid, C::NT + 32, L::total(p.stages, mode), s>>>(p);
+  DAMN_CHECK_LAUNCH("k_spmv");
+  return DAMN_OK;
+}
+
+template <bool PLAIN, typename V, typename I, class C>
+int launch_band(SpmvParams p, cudaStream_t s, int *gs_out) {
+  using L = BandLayout<V, I, C>;
+  static Occ cache[kMaxDev];
+  static std::mutex mu;
+  int st = 2, occ = 1;
+  int rc = pick_geometry(k_spmv_band<PLAIN, V, I, C>, C::G * C::NT + 32,
+                         [](int k) { return L::total(k); }, 1, p.stages_req, cache, mu, &st, &occ);
+  if (rc) return rc;
+  p.stages = st;
+  // one chunk of consecutive tiles per CTA; at least a few tiles per chunk
+  const int grid = std::max(1, std::min(occ * sm_count(), (p.ntiles + 3) / 4));
+  if (gs_out) { gs_out[0] = grid; gs_out[1] = p.stages; }
+  if (p.ntiles == 0) return DAMN_OK;
+  k_spmv_band<PLAIN, V, I, C><<<grid, C::G * C::NT + 32, L::total(p.stages), s>>>(p);
+  DAMN_CHECK_LAUNCH("k_spmv_band");
+  return DAMN_OK;
+}
+
+inline bool is_plain(const SpmvParams &p) {
+  return p.ab_mode == 0 && !p.dot_w && !p.dot_self && !p.dot_partials;
+}
+
+template <typename V, typename I, class C>
+int launch_cfg(const SpmvParams &p, cudaStream_t s, int *gs) {
+  const bool plain = is_plain(p);
+  // one row per lane with every x window of at most 3 segments: one compare
+  // fewer per entry in the column -> slot map
+  if constexpr (C::E == 1) {
+    if (p.mode == 0 && p.max_nseg <= 3) {
+      if (plain) return launch_kernel<true, V, I, C, 3>(p, s, gs);
+      return launch_kernel<false, V, I, C, 3>(p, s, gs);
+    }
+  }
+  if (plain) return launch_kernel<true, V, I, C, kXSegMax>(p, s, gs);
+  return launch_kernel<false, V, I, C, kXSegMax>(p, s, gs);
+}
+
+template <typename V, typename I>
+int launch_types(const SpmvParams &p, int shape, cudaStream_t s, int *gs) {
+  using CB = std::conditional_t<sizeof(V) == 8, CfgBand64, CfgBand32>;
+  switch (shape) {
+    case kShapeLong: return launch_cfg<V, I, CfgLong>(p, s, gs);
+    case kShapeSlices: return launch_cfg<V, I, CfgSlices>(p, s, gs);
+    case kShapeBand:
+      return is_plain(p) ? launch_band<true, V, I, CB>(p, s, gs)
+                         : launch_band<false, V, I, CB>(p, s, gs);
+    case kShapeLanes4: return launch_cfg<V, I, CfgLanes4>(p, s, gs);
+    case kShapeLanes8: return launch_cfg<V, I, CfgLanes8>(p, s, gs);
+    case kShapeLanes16: return launch_cfg<V, I, CfgLanes16>(p, s, gs);
+    case kShapeLanes32: return launch_cfg<V, I, CfgLanes32>(p, s, gs);
+    default: break;
+  }
+  if constexpr (sizeof(V) < 8)
+    return launch_cfg<V, I, CfgShortNarrow>(p, s, gs);
+  else
+    return launch_cfg<V, I, CfgShort>(p, s, gs);
+}
+
+}  // namespace spmvk
+}  // namespace damn
+
+// Defines the launcher of one (value type, index type) pair.
+#define DAMN_SPMV_INSTANCE(NAME, V, I)                                                   \
+  namespace damn {                                                                      \
+  int NAME(const spmvk::SpmvParams &p, int shape, cudaStream_t s, int *gs) {            \
+    return spmvk::launch_types<V, I>(p, shape, s, gs);                                  \
+  }                                                                                     \
+  }

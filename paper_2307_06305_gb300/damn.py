@@ -28,7 +28,9 @@ DAMN_ERR_UNSUPPORTED = -6
 
 DAMN_F64, DAMN_F32, DAMN_BF16 = 0, 1, 2
 DAMN_FMT_CSR32, DAMN_FMT_DACSR16, DAMN_FMT_DACSR8 = 0, 1, 2
-DAMN_TILING_SLICES, DAMN_TILING_ROWS, DAMN_TILING_ROWS_LONG = 0, 1, 2
+DAMN_TILING_SLICES, DAMN_TILING_ROWS, DAMN_TILING_ROWS_LONG, DAMN_TILING_BAND = 0, 1, 2, 3
+DAMN_TILING_ROWS_LANES4, DAMN_TILING_ROWS_LANES8 = 4, 5
+DAMN_TILING_ROWS_LANES16, DAMN_TILING_ROWS_LANES32 = 6, 7
 
 _DTYPE_CODE = {torch.float64: DAMN_F64, torch.float32: DAMN_F32, torch.bfloat16: DAMN_BF16}
 _VEC_DTYPE = {DAMN_F64: torch.float64, DAMN_F32: torch.float32, DAMN_BF16: torch.float32}
@@ -65,7 +67,8 @@ class damn_bw_info(ctypes.Structure):
 class damn_plan_desc(ctypes.Structure):
     _fields_ = [("mode", I32), ("tile_items", I32), ("ntiles", I32), ("grid", I32),
                 ("stages", I32), ("threads", I32), ("row_efficiency", F64), ("max_row", I32),
-                ("dtype", I32), ("tiling", I32), ("x_staged_tiles", I32)]
+                ("dtype", I32), ("tiling", I32), ("x_staged_tiles", I32),
+                ("stages_requested", I32)]
 
 
 class damn_cg_result(ctypes.Structure):
@@ -111,6 +114,7 @@ _sig("damn_plan_create", ctypes.c_int,
 _sig("damn_plan_autotune", ctypes.c_int, [P, ctypes.c_int, P, P, P, P, P])
 _sig("damn_plan_describe", ctypes.c_int, [P, ctypes.POINTER(damn_plan_desc)])
 _sig("damn_plan_set_tiling", ctypes.c_int, [P, ctypes.c_int])
+_sig("damn_plan_set_stages", ctypes.c_int, [P, I32])
 _sig("damn_plan_destroy", ctypes.c_int, [P])
 _sig("damn_spmv_csr32", ctypes.c_int,
      [I32, I32, I64, P, P, P, ctypes.c_int, P, P, F64, F64, P, P])
@@ -325,6 +329,11 @@ class Plan:
 
     def set_tiling(self, tiling: int):
         _check(_lib.damn_plan_set_tiling(self.handle, int(tiling)), "damn_plan_set_tiling")
+        return self
+
+    def set_stages(self, stages: int):
+        """Ring depth of the plan's launches (0: automatic, else 2..8)."""
+        _check(_lib.damn_plan_set_stages(self.handle, int(stages)), "damn_plan_set_stages")
         return self
 
     def describe(self) -> dict:

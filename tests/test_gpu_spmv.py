@@ -22,7 +22,8 @@ pytestmark = pytest.mark.gpu
 
 # plan variants: no plan; heuristic plan with x windows from off or from col;
 # each tiling pinned (x windows from off); a plan without x windows (x gathered)
-MODES = ["none", "auto", "auto_col", "rows", "rows_long", "slices", "rows_gather"]
+MODES = ["none", "auto", "auto_col", "rows", "rows_long", "slices", "rows_gather", "band",
+         "band_col", "band_gather", "lanes4", "lanes8", "lanes16", "lanes32"]
 
 
 def _t(dev, a):
@@ -34,6 +35,8 @@ class Mat:
         self.nrows, self.ncols = nrows, ncols
         self.rp, self.col, self.val = rp, col, val
         self.off = OD.translate(nrows, rp, col)
+        # DA-CSR-16 input must fit int16 (a wrapped offset addresses another column)
+        assert self.off.size == 0 or (self.off.min() >= -32768 and self.off.max() <= 32767)
         self.t_rp = _t(dev, rp)
         self.t_col = _t(dev, col)
         self.t_off = _t(dev, self.off.astype(np.int16))
@@ -45,10 +48,15 @@ class Mat:
 def _plan(D, m, mode):
     if mode == "none":
         return None
-    idx = {"auto_col": m.t_col, "rows_gather": None}.get(mode, m.t_off)
+    idx = {"auto_col": m.t_col, "band_col": m.t_col, "rows_gather": None,
+           "band_gather": None}.get(mode, m.t_off)
     p = D.Plan(m.t_rp, len(m.col), m.ncols, m.dtype, idx=idx)
     tiling = {"rows": D.DAMN_TILING_ROWS, "rows_long": D.DAMN_TILING_ROWS_LONG,
-              "slices": D.DAMN_TILING_SLICES, "rows_gather": D.DAMN_TILING_ROWS}.get(mode)
+              "slices": D.DAMN_TILING_SLICES, "rows_gather": D.DAMN_TILING_ROWS,
+              "band": D.DAMN_TILING_BAND, "band_col": D.DAMN_TILING_BAND,
+              "band_gather": D.DAMN_TILING_BAND, "lanes4": D.DAMN_TILING_ROWS_LANES4,
+              "lanes8": D.DAMN_TILING_ROWS_LANES8, "lanes16": D.DAMN_TILING_ROWS_LANES16,
+              "lanes32": D.DAMN_TILING_ROWS_LANES32}.get(mode)
     if tiling is not None:
         p.set_tiling(tiling)
     return p
@@ -246,12 +254,11 @@ def test_device_status_clean(D, cuda_dev):
     assert D.damn_device_status() == 0
 
 
-@pytest.mark.parametrize("h,expect", [(100, "rows_long"), (5000, "slices")])
-def test_heuristic_ragged_rows(D, cuda_dev, h, expect):
+@pytest.mark.parametrize("h", [100, 5000])
+def test_heuristic_ragged_rows(D, cuda_dev, h):
     """Random banded rows (lengths LogNormal around 12, row efficiency about
-    0.4): the plan runs them two lanes per row when the 128-row tiles' x
-    windows are staged (narrow band), as balanced slices when they are not
-    (wide band); either way within the bound and CSR-32 == DA-CSR-16."""
+    0.4) get the band tiling (entry-balanced slices) whatever the band width;
+    within the bound and CSR-32 == DA-CSR-16."""
     rng = np.random.default_rng(21)
     n = 20000
     rp, col, val = W.random_banded(n, h, rng)
@@ -259,39 +266,105 @@ def test_heuristic_ragged_rows(D, cuda_dev, h, expect):
     plan = D.Plan(m.t_rp, len(m.col), n, torch.float64, idx=m.t_off)
     d = plan.describe()
     assert 0.3 <= d["row_efficiency"] < 0.85
-    want = {"rows_long": D.DAMN_TILING_ROWS_LONG, "slices": D.DAMN_TILING_SLICES}[expect]
-    assert d["tiling"] == want, d
-    if expect == "rows_long":
-        assert d["x_staged_tiles"] >= 0.9 * d["ntiles"]
+    assert d["tiling"] == D.DAMN_TILING_BAND, d
     x = W.uniform_vector(n, rng)
     got = _run(D, m, x, plan=plan)
     _bound_check(m, x, got)
     assert np.array_equal(got, _run(D, m, x, plan=plan, fmt="csr"))
 
 
-def test_plan_rejects_other_arrays(D, cuda_dev):
-    """A plan's tiles and x windows belong to the arrays it was built from:
-    a call with another rowptr, or another index array of the plan's own
-    format, is refused before any device work (a different pattern would
-    read rows and x slots the plan never prepared); the CSR-32 copy of the
-    same matrix is accepted under a plan built from its DA-CSR-16 offsets."""
-    rng = np.random.default_rng(31)
-    n = 3000
-    rp, col, val = W.random_banded(n, 50, rng)
+@pytest.mark.parametrize("lanes,length", [(1, 7), (2, 20), (4, 50), (8, 100), (16, 200),
+                                          (32, 400)])
+def test_heuristic_uniform_rows_lanes(D, cuda_dev, lanes, length):
+    """Uniform rows get the fewest lanes per row that keep <= 7 (one lane)
+    or <= 14 entries per lane."""
+    n = 4000
+    rows = np.repeat(np.arange(n), length)
+    cols = (rows + np.tile(np.arange(length) - length // 2, n)) % n
+    rp, col, val = W.from_coo(n, rows, cols, np.random.default_rng(3).standard_normal(len(rows)))
     m = Mat(D, cuda_dev, n, n, rp, col, val)
     plan = D.Plan(m.t_rp, len(col), n, torch.float64, idx=m.t_off)
-    x = _t(cuda_dev, W.uniform_vector(n, rng))
-    y = torch.zeros(n, dtype=torch.float64, device=cuda_dev)
-    other_rp = m.t_rp.clone()
-    other_off = m.t_off.clone()
-    f = D._lib.damn_spmv_dacsr16
-    rc = f(n, n, len(col), D._ptr(other_rp), D._ptr(m.t_off), D._ptr(m.t_val), D.DAMN_F64,
-           D._ptr(x), D._ptr(y), 1.0, 0.0, plan.handle, D._stream())
-    assert rc == D.DAMN_ERR_INVALID_ARG and "rowptr" in D.last_error()
-    rc = f(n, n, len(col), D._ptr(m.t_rp), D._ptr(other_off), D._ptr(m.t_val), D.DAMN_F64,
-           D._ptr(x), D._ptr(y), 1.0, 0.0, plan.handle, D._stream())
-    assert rc == D.DAMN_ERR_INVALID_ARG and "index array" in D.last_error()
-    # the CSR-32 copy of the same matrix under the DA-CSR-16 plan: accepted
-    D.damn_spmv_csr32(m.t_rp, m.t_col, m.t_val, x, y, plan=plan)
-    torch.cuda.synchronize()
-    assert D.damn_device_status() == 0
+    want = {1: D.DAMN_TILING_ROWS, 2: D.DAMN_TILING_ROWS_LONG, 4: D.DAMN_TILING_ROWS_LANES4,
+            8: D.DAMN_TILING_ROWS_LANES8, 16: D.DAMN_TILING_ROWS_LANES16,
+            32: D.DAMN_TILING_ROWS_LANES32}[lanes]
+    assert plan.describe()["tiling"] == want
+    x = W.uniform_vector(n, np.random.default_rng(4))
+    got = _run(D, m, x, plan=plan)
+    _bound_check(m, x, got)
+    assert np.array_equal(got, _run(D, m, x, plan=plan, fmt="csr"))
+
+
+@pytest.mark.parametrize("stages", [2, 3, 4, 6])
+@pytest.mark.parametrize("tiling", ["band", "rows", "lanes4", "slices"])
+def test_ring_depths(D, cuda_dev, tiling, stages):
+    """Every ring depth gives the same bits as the automatic depth (the
+    summation order does not depend on it)."""
+    rng = np.random.default_rng(40 + stages)
+    n = 30000
+    rp, col, val = W.random_banded(n, 700, rng)
+    m = Mat(D, cuda_dev, n, n, rp, col, val)
+    x = W.uniform_vector(n, rng)
+    plan = _plan(D, m, tiling)
+    ref = _run(D, m, x, plan=plan)
+    plan.set_stages(stages)
+    got = _run(D, m, x, plan=plan)
+    assert np.array_equal(got, ref)
+    assert plan.describe()["stages_requested"] == stages
+    _bound_check(m, x, got)
+
+
+@pytest.mark.parametrize("h", [300, 2000, 3500, 6000, 30000])
+def test_band_ring_and_gather(D, cuda_dev, h):
+    """Band tiling across band widths: x from the ring (narrow bands), partly
+    or wholly gathered (bands the 8192-slot ring cannot hold); results within
+    the bound, bitwise equal for CSR-32 / DA-CSR-16 and for FP32 values
+    between the two formats."""
+    rng = np.random.default_rng(h)
+    n = 60000
+    rp, col, val = W.random_banded(n, h, rng)
+    m = Mat(D, cuda_dev, n, n, rp, col, val)
+    x = W.uniform_vector(n, rng)
+    plan = _plan(D, m, "band")
+    got = _run(D, m, x, plan=plan)
+    _bound_check(m, x, got)
+    assert np.array_equal(got, _run(D, m, x, plan=plan, fmt="csr"))
+    y0 = rng.standard_normal(n)
+    got = _run(D, m, x, y0, -0.5, 2.0, plan=plan)
+    _bound_check(m, x, got, y0, -0.5, 2.0)
+    m32 = Mat(D, cuda_dev, n, n, rp, col, val, torch.float32)
+    p32 = _plan(D, m32, "band")
+    g32 = _run(D, m32, x.astype(np.float32), plan=p32)
+    assert np.array_equal(g32, _run(D, m32, x.astype(np.float32), plan=p32, fmt="csr"))
+
+
+def test_band_outliers_and_nonsquare(D, cuda_dev):
+    """Rows with an entry far from the diagonal (their tiles gather x, the
+    ring restarts after them), a tall and a wide matrix, and rows longer
+    than a stage (tiles read from global memory)."""
+    rng = np.random.default_rng(77)
+    n = 50000
+    rp, col, val = W.random_banded(n, 200, rng)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    far_r = rng.integers(0, n, 40)
+    far_c = (far_r + n // 2) % n
+    long_r = np.full(5000, 1234)
+    long_c = rng.integers(0, 1234 + 30000, 5000)   # offsets within int16
+    rr = np.concatenate([rows, far_r, long_r])
+    cc = np.concatenate([col, far_c, long_c])
+    rp2, col2, val2 = W.from_coo(n, rr, cc, rng.standard_normal(len(rr)))
+    assert OD.fit_check(n, n, rp2, col2).fits
+    m = Mat(D, cuda_dev, n, n, rp2, col2, val2)
+    x = W.uniform_vector(n, rng)
+    for mode in ("band", "band_col", "band_gather"):
+        plan = _plan(D, m, mode)
+        got = _run(D, m, x, plan=plan)
+        _bound_check(m, x, got)
+        assert np.array_equal(got, _run(D, m, x, plan=plan, fmt="csr"))
+    for nr, nc in ((30000, 9000), (9000, 30000)):
+        rpn, coln, valn = W.random_banded_rect(nr, nc, 400, rng)
+        mn = Mat(D, cuda_dev, nr, nc, rpn, coln, valn)
+        xn = W.uniform_vector(nc, rng)
+        plan = _plan(D, mn, "band")
+        got = _run(D, mn, xn, plan=plan)
+        _bound_check(mn, xn, got)
+        assert np.array_equal(got, _run(D, mn, xn, plan=plan, fmt="csr"))

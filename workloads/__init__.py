@@ -292,6 +292,25 @@ def random_banded(n: int, h: int, rng: np.random.Generator, median: float = 12.0
     return rowptr.astype(np.int32), col, val
 
 
+def random_banded_rect(nrows: int, ncols: int, h: int, rng: np.random.Generator,
+                       median: float = 12.0, sigma: float = 0.5):
+    """Seeded random banded nrows x ncols matrix: row r draws its entries
+    (count as in ``random_banded``) uniformly from the columns within h of r
+    that exist, [max(0, r - h), min(ncols - 1, r + h)]; rows whose window is
+    empty (r - h >= ncols) stay empty.  Values N(0, 1)."""
+    k = np.clip(np.rint(rng.lognormal(np.log(median), sigma, size=nrows)), 1, 200).astype(np.int64)
+    r = np.arange(nrows, dtype=np.int64)
+    lo = np.maximum(0, r - h)
+    hi = np.minimum(ncols - 1, r + h)
+    ok = hi >= lo
+    k = np.where(ok, k, 0)
+    rr = np.repeat(r, k)
+    cols = lo[rr] + rng.integers(0, (hi - lo + 1)[rr])
+    key = np.unique(rr * ncols + cols)
+    rows_u, cols_u = key // ncols, key % ncols
+    return from_coo(nrows, rows_u, cols_u, rng.standard_normal(len(key)))
+
+
 def batch_banded(count: int = 512, seed: int | None = None, n_median: float = 14142.0,
                  n_sigma: float = 1.0, n_min: int = 1000, n_max: int = 200000,
                  k_min: int = 5, k_max: int = 40, h_min: int = 16, h_max: int = 4096):
