@@ -655,8 +655,8 @@ BANDED_POINTS_FULL = tuple((n, h) for n in (100_000, 300_000, 1_000_000, 3_000_0
                                             20_000_000) for h in (100, 1000, 30000))
 L2_BYTES = 126e6
 TILING_NAMES = ("slices", "rows", "rows_long", "band", "lanes4", "lanes8", "lanes16",
-                "lanes32")   # DAMN_TILING_* 0 .. 7
-BANDED_TILINGS = (0, 1, 2, 3, 4)  # the tilings timed in the banded section
+                "lanes32", "sorted")   # DAMN_TILING_* 0 .. 8
+BANDED_TILINGS = (0, 2, 3, 8)  # the tilings timed in the banded section
 
 
 def section_banded(D, torch, dev, reps, full=False):

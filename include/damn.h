@@ -237,6 +237,7 @@ typedef struct {
 #define DAMN_TILING_ROWS_LANES8   5
 #define DAMN_TILING_ROWS_LANES16  6
 #define DAMN_TILING_ROWS_LANES32  7
+#define DAMN_TILING_SORTED_ROWS   8
 
 /* Builds a plan for one matrix and value dtype: the partition of the rows
  * into tiles and the compute mode (the tiling), chosen from the row-length
@@ -281,14 +282,22 @@ int damn_plan_autotune(damn_plan *plan, int format, const void *idx, const void 
  *  DAMN_TILING_BAND: the same balanced tiles and slices, each CTA walking a
  *    contiguous run of tiles with x in a shared-memory ring (column c in slot
  *    c mod W, W = 8192 for FP64 x, 16384 for FP32 x); a tile whose columns
- *    the ring cannot hold reads x from global memory.
+ *    the ring cannot hold reads x from global memory;
+ *  DAMN_TILING_SORTED_ROWS: tiles of 192 rows, each CTA walking a contiguous
+ *    run of tiles with x in a ring (W = 4096 for FP64 x, 8192 for FP32 x);
+ *    one row per thread, the tile's rows dealt to threads in order of
+ *    decreasing length (a permutation the plan computes), so a warp's rows
+ *    have similar lengths; rows longer than 128 entries are summed by a
+ *    whole warp (lane-strided partial sums added by a butterfly).
  * Recomputes the staging data; synchronises the legacy default stream. */
 int damn_plan_set_tiling(damn_plan *plan, int tiling);
 
 /* Ring depth (shared-memory stages per CTA) of the plan's SpMV launches:
  * 0 = automatic (the deepest ring that keeps the kernel's CTAs per SM), or
  * 2 .. 8; a depth that does not fit the kernel's shared memory falls back to
- * automatic.  No device work. */
+ * automatic.  The band and sorted-rows tilings run several consumer groups
+ * that take turns on the tiles; their depth is rounded down to a multiple of
+ * the number of groups (4 and 2).  No device work. */
 int damn_plan_set_stages(damn_plan *plan, int32_t stages);
 
 int damn_plan_describe(const damn_plan *plan, damn_plan_desc *h_desc);

@@ -305,6 +305,54 @@ k_plan_colrange(const int *__restrict__ rowptr, const void *idx, int fmt, int nt
   }
 }
 
+// Bounds of fixed tiles of tile_rows rows: {first row, rowptr[first row]}.
+__global__ void k_plan_fixed_bounds(int nrows, const int *__restrict__ rowptr, int tile_rows,
+                                    int ntiles, int2 *bounds) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > ntiles) return;
+  const int r = (int)min((long long)t * tile_rows, (long long)nrows);
+  bounds[t] = make_int2(r, rowptr[r]);
+}
+
+// Rows of every tile of tile_rows (<= 1024) rows in order of decreasing
+// length, equal lengths by increasing index (a bitonic sort of 1024 keys per
+// block): perm[t * tile_rows + i] = tile-local index of the i-th longest row.
+__global__ void __launch_bounds__(512)
+k_plan_sortrows(int nrows, const int *__restrict__ rowptr, int tile_rows, int ntiles,
+                uint16_t *perm) {
+  __shared__ unsigned keys[1024];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int r0 = t * tile_rows;
+    const int nr = min(tile_rows, nrows - r0);
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+      unsigned k = 0;  // padding sorts last
+      if (i < nr) {
+        const unsigned len = (unsigned)min(rowptr[r0 + i + 1] - rowptr[r0 + i], (1 << 21) - 1);
+        k = (len << 10) | (1023u - (unsigned)i);
+      }
+      keys[i] = k;
+    }
+    __syncthreads();
+    for (int size = 2; size <= 1024; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+          const int jx = i ^ stride;
+          if (jx > i) {
+            const bool down = (i & size) == 0;  // descending overall
+            const unsigned a = keys[i], b = keys[jx];
+            if ((a < b) == down) { keys[i] = b; keys[jx] = a; }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int i = threadIdx.x; i < tile_rows; i += blockDim.x)
+      perm[(long long)t * tile_rows + i] =
+          i < nr ? (uint16_t)(1023u - (keys[i] & 1023u)) : (uint16_t)0;
+    __syncthreads();
+  }
+}
+
 // Most entries of any tile of tile_rows consecutive rows (*out, atomicMax).
 __global__ void k_plan_max_tile(int nrows, const int *__restrict__ rowptr, int tile_rows, int *out) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -324,7 +372,7 @@ struct damn_plan {
   const int32_t *rowptr;  // caller's arrays (kept for the autotuner and the x windows)
   const void *idx;        // column indices (may be NULL: no x windows)
   int fmt;
-  int mode;               // 0 rows, 1 balanced slices, 2 band
+  int mode;               // 0 rows, 1 balanced slices, 2 band, 3 sorted rows
   int shape;              // kernel configuration (spmvk::Shape)
   int rows_per_tile;      // > 0 fixed row tiles, 0 bounds
   int ntiles;
@@ -334,6 +382,10 @@ struct damn_plan {
   XSeg *d_xseg;           // x windows of the current tiling (NULL: none)
   int xseg_cap;
   int2 *d_colrange;       // band mode: column range of every balanced tile (NULL: none)
+  int ntiles_sorted;      // sorted-rows tiling: fixed tiles, their bounds, column
+  int2 *d_bounds_sorted;  // ranges and row permutation (built on first use)
+  int2 *d_colrange_sorted;
+  uint16_t *d_perm;
   int staged_tiles;
   int max_nseg;           // most x segments of a tile's window (rows mode kernel variant)
   int max_row;
@@ -363,6 +415,10 @@ static CfgGeom cfg_geom(int shape, int dtype) {
     case kShapeLanes8: return {CfgLanes8::TILE_ROWS, CfgLanes8::CAP_NZ, CfgLanes8::XCAP, 256};
     case kShapeLanes16: return {CfgLanes16::TILE_ROWS, CfgLanes16::CAP_NZ, CfgLanes16::XCAP, 256};
     case kShapeLanes32: return {CfgLanes32::TILE_ROWS, CfgLanes32::CAP_NZ, CfgLanes32::XCAP, 256};
+    case kShapeSorted:
+      return {CfgSorted64::NT, CfgSorted64::CAP_NZ,
+              dtype == DAMN_F64 ? CfgSorted64::W : CfgSorted32::W,
+              CfgSorted64::G * CfgSorted64::NT};
     default: break;
   }
   if (dtype != DAMN_F64)
@@ -381,6 +437,7 @@ static int shape_of_tiling(int tiling) {
     case DAMN_TILING_ROWS_LANES8: return kShapeLanes8;
     case DAMN_TILING_ROWS_LANES16: return kShapeLanes16;
     case DAMN_TILING_ROWS_LANES32: return kShapeLanes32;
+    case DAMN_TILING_SORTED_ROWS: return kShapeSorted;
     default: return -1;
   }
 }
@@ -393,6 +450,7 @@ static int tiling_of_shape(int shape) {
     case kShapeLanes8: return DAMN_TILING_ROWS_LANES8;
     case kShapeLanes16: return DAMN_TILING_ROWS_LANES16;
     case kShapeLanes32: return DAMN_TILING_ROWS_LANES32;
+    case kShapeSorted: return DAMN_TILING_SORTED_ROWS;
     default: return DAMN_TILING_ROWS;
   }
 }
@@ -422,8 +480,10 @@ static int make_params(const SpmvCall &c, const damn_plan *plan, SpmvParams &p, 
     p.rows_per_tile = plan->rows_per_tile;
     p.ntiles = plan->ntiles;
     p.bounds = plan->d_bounds;
-    p.xseg = plan->mode == 2 ? nullptr : plan->d_xseg;
-    p.colrange = plan->mode == 2 ? plan->d_colrange : nullptr;
+    p.xseg = plan->mode >= 2 ? nullptr : plan->d_xseg;
+    p.colrange = plan->mode == 2 ? plan->d_colrange
+                 : plan->mode == 3 ? plan->d_colrange_sorted : nullptr;
+    p.perm = plan->mode == 3 ? plan->d_perm : nullptr;
     p.stages_req = plan->stages_req;
     p.max_nseg = p.xseg ? plan->max_nseg : kXSegMax;
     shape = plan->shape;
@@ -537,6 +597,12 @@ static void plan_free_device(damn_plan *pl) {
   if (pl->d_bounds_balanced) cudaFree(pl->d_bounds_balanced);
   if (pl->d_xseg) cudaFree(pl->d_xseg);
   if (pl->d_colrange) cudaFree(pl->d_colrange);
+  if (pl->d_bounds_sorted) cudaFree(pl->d_bounds_sorted);
+  if (pl->d_colrange_sorted) cudaFree(pl->d_colrange_sorted);
+  if (pl->d_perm) cudaFree(pl->d_perm);
+  pl->d_bounds_sorted = nullptr;
+  pl->d_colrange_sorted = nullptr;
+  pl->d_perm = nullptr;
   pl->d_bounds_balanced = nullptr;
   pl->d_xseg = nullptr;
   pl->d_colrange = nullptr;
@@ -589,9 +655,44 @@ static int plan_colrange(damn_plan *pl, cudaStream_t s) {
   return DAMN_OK;
 }
 
+// Fixed tiles (CfgSorted64::NT rows), their column ranges and row permutations, for the
+// sorted-rows tiling (once per plan; synchronises).
+static int plan_sorted(damn_plan *pl, cudaStream_t s) {
+  if (pl->d_perm || pl->nrows == 0) return DAMN_OK;
+  const int tr = CfgSorted64::NT;
+  const int nt = (pl->nrows + tr - 1) / tr;
+  DAMN_CUDA(cudaMalloc(&pl->d_bounds_sorted, sizeof(int2) * (size_t)(nt + 1)));
+  DAMN_CUDA(cudaMalloc(&pl->d_perm, sizeof(uint16_t) * (size_t)nt * tr));
+  k_plan_fixed_bounds<<<(nt + 1 + 255) / 256, 256, 0, s>>>(pl->nrows, pl->rowptr, tr, nt,
+                                                            pl->d_bounds_sorted);
+  k_plan_sortrows<<<std::min(nt, 16 * sm_count()), 512, 0, s>>>(pl->nrows, pl->rowptr, tr, nt,
+                                                                pl->d_perm);
+  DAMN_CHECK_LAUNCH("k_plan_sortrows");
+  if (pl->idx) {
+    DAMN_CUDA(cudaMalloc(&pl->d_colrange_sorted, sizeof(int2) * (size_t)nt));
+    k_plan_colrange<<<std::min(nt, 16 * sm_count()), 256, 0, s>>>(
+        pl->rowptr, pl->idx, pl->fmt, nt, pl->d_bounds_sorted, pl->d_colrange_sorted);
+    DAMN_CHECK_LAUNCH("k_plan_colrange");
+  }
+  pl->ntiles_sorted = nt;
+  DAMN_CUDA(cudaStreamSynchronize(s));
+  return DAMN_OK;
+}
+
 static int plan_use(damn_plan *pl, int tiling, cudaStream_t s) {
   const int shape = shape_of_tiling(tiling);
   pl->shape = shape;
+  if (shape == kShapeSorted) {
+    int rc = plan_sorted(pl, s);
+    if (rc) return rc;
+    pl->mode = 3;
+    pl->rows_per_tile = 0;
+    pl->ntiles = pl->ntiles_sorted;
+    pl->d_bounds = pl->d_bounds_sorted;
+    pl->staged_tiles = 0;
+    pl->max_nseg = kXSegMax;
+    return DAMN_OK;
+  }
   if (shape == kShapeSlices || shape == kShapeBand) {
     pl->mode = shape == kShapeBand ? 2 : 1;
     pl->rows_per_tile = 0;
@@ -699,10 +800,11 @@ extern "C" int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const
   pl->row_eff = h.sum_group_max ? (double)nnz / (32.0 * (double)h.sum_group_max) : 1.0;
   // Heuristic choice.  Rows of uniform length inside 32-row groups: rows
   // mode with the fewest lanes per row that keep a row's entries in
-  // registers.  Ragged rows: band mode -- entry-balanced slices (a full warp
-  // of entries per FMA whatever the row lengths), x through the ring when
-  // the band is narrow enough and gathered otherwise.
-  int tiling = DAMN_TILING_BAND;
+  // registers.  Ragged rows: the sorted-rows tiling -- rows dealt to the
+  // threads of a tile by decreasing length, so a warp's FMA steps carry
+  // nearly full lanes, x through the ring when the band is narrow enough and
+  // gathered otherwise.
+  int tiling = DAMN_TILING_SORTED_ROWS;
   int rc = DAMN_OK;
   if (pl->row_eff >= 0.85) {
     int t = -1;
@@ -752,11 +854,12 @@ extern "C" int damn_plan_autotune(damn_plan *plan, int format, const void *idx, 
   // 1. tilings: the fixed shapes, and the lanes-per-row tilings whose lanes
   //    would each hold at least two entries of an average row
   const double mean = (double)plan->nnz / plan->nrows;
-  int cands[8], nc = 0;
+  int cands[9], nc = 0;
   cands[nc++] = DAMN_TILING_ROWS;
   cands[nc++] = DAMN_TILING_ROWS_LONG;
   cands[nc++] = DAMN_TILING_SLICES;
   cands[nc++] = DAMN_TILING_BAND;
+  cands[nc++] = DAMN_TILING_SORTED_ROWS;
   const int lane_t[4] = {DAMN_TILING_ROWS_LANES4, DAMN_TILING_ROWS_LANES8, DAMN_TILING_ROWS_LANES16,
                          DAMN_TILING_ROWS_LANES32};
   for (int i = 0; i < 4; ++i)
@@ -806,7 +909,9 @@ extern "C" int damn_plan_set_stages(damn_plan *plan, int32_t stages) {
 extern "C" int damn_plan_describe(const damn_plan *plan, damn_plan_desc *h_desc) {
   if (!plan || !h_desc) return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_describe: NULL");
   h_desc->mode = plan->mode;
-  h_desc->tile_items = plan->rows_per_tile > 0 ? plan->rows_per_tile : kBalancedItems;
+  h_desc->tile_items = plan->rows_per_tile > 0    ? plan->rows_per_tile
+                       : plan->shape == kShapeSorted ? CfgSorted64::NT
+                                                     : kBalancedItems;
   h_desc->ntiles = plan->ntiles;
   h_desc->grid = plan->grid;
   h_desc->stages = plan->stages;

@@ -115,6 +115,7 @@ struct SpmvParams {
   int stages_req;      // requested depth (0: the deepest that keeps MINB CTAs per SM)
   int max_nseg;        // most x segments of any tile's window
   const int2 *colrange;  // band mode: {min, max} column of every tile (NULL: none)
+  const uint16_t *perm;  // sorted-rows mode: tile-local rows by decreasing length
   int *status;
   unsigned long long timeout_ns;
 };
@@ -173,6 +174,7 @@ enum Shape {
   kShapeLanes8 = 5,
   kShapeLanes16 = 6,
   kShapeLanes32 = 7,
+  kShapeSorted = 8,  // row tiles sorted by length, one row per thread, x ring
 };
 
 constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

@@ -24,10 +24,16 @@ struct Occ {
 };
 
 // Ring depth and CTAs per SM: the requested depth when it fits, else the
-// deepest ring that keeps `minb` CTAs per SM (at least two stages).
+// deepest ring that keeps `minb` CTAs per SM (at least two stages).  Kernels
+// whose consumer groups take turns on the tiles (band, sorted rows) need a
+// depth that is a multiple of the number of groups `mult`: then stage s is
+// only ever reused by the group that consumed it last, so a group waiting
+// for a stage's next phase is never two phases behind it (a parity wait
+// would otherwise take an older completed phase of the same parity for the
+// one it wants).  A requested depth is rounded down to such a multiple.
 template <class KFn, class TotalFn>
 int pick_geometry(KFn kernel, int threads, TotalFn total, int minb, int req, Occ (&cache)[kMaxDev],
-                  std::mutex &mu, int *stages, int *occ) {
+                  std::mutex &mu, int *stages, int *occ, int mult = 1) {
   int dev = 0;
   DAMN_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDev) return set_error(DAMN_ERR_UNSUPPORTED, "device index too large");
@@ -45,13 +51,16 @@ int pick_geometry(KFn kernel, int threads, TotalFn total, int minb, int req, Occ
     }
     c.known = 1;
   }
-  if (req >= 2 && req <= kMaxStages && c.occ[req] > 0) {
+  const int lo = mult > 2 ? mult : 2;
+  if (req > 0) req = req / mult * mult;
+  if (req >= lo && req <= kMaxStages && c.occ[req] > 0) {
     *stages = req;
     *occ = c.occ[req];
     return DAMN_OK;
   }
-  int best_s = 2, best_o = 0;
-  for (int st = kMaxStages; st >= 2; --st) {
+  int best_s = lo, best_o = 0;
+  for (int st = kMaxStages; st >= lo; --st) {
+    if (st % mult) continue;
     if (c.occ[st] >= minb) { best_s = st; best_o = c.occ[st]; break; }
     if (c.occ[st] > best_o) { best_s = st; best_o = c.occ[st]; }
   }
@@ -88,7 +97,8 @@ int launch_band(SpmvParams p, cudaStream_t s, int *gs_out) {
   static std::mutex mu;
   int st = 2, occ = 1;
   int rc = pick_geometry(k_spmv_band<PLAIN, V, I, C>, C::G * C::NT + 32,
-                         [](int k) { return L::total(k); }, 1, p.stages_req, cache, mu, &st, &occ);
+                         [](int k) { return L::total(k); }, 1, p.stages_req, cache, mu, &st, &occ,
+                         C::G);
   if (rc) return rc;
   p.stages = st;
   // one chunk of consecutive tiles per CTA; at least a few tiles per chunk
@@ -97,6 +107,25 @@ int launch_band(SpmvParams p, cudaStream_t s, int *gs_out) {
   if (p.ntiles == 0) return DAMN_OK;
   k_spmv_band<PLAIN, V, I, C><<<grid, C::G * C::NT + 32, L::total(p.stages), s>>>(p);
   DAMN_CHECK_LAUNCH("k_spmv_band");
+  return DAMN_OK;
+}
+
+template <bool PLAIN, typename V, typename I, class C>
+int launch_sorted(SpmvParams p, cudaStream_t s, int *gs_out) {
+  using L = BandLayout<V, I, C>;
+  static Occ cache[kMaxDev];
+  static std::mutex mu;
+  int st = 2, occ = 1;
+  int rc = pick_geometry(k_spmv_sorted<PLAIN, V, I, C>, C::G * C::NT + 32,
+                         [](int k) { return L::total(k); }, 1, p.stages_req, cache, mu, &st, &occ,
+                         C::G);
+  if (rc) return rc;
+  p.stages = st;
+  const int grid = std::max(1, std::min(occ * sm_count(), (p.ntiles + 3) / 4));
+  if (gs_out) { gs_out[0] = grid; gs_out[1] = p.stages; }
+  if (p.ntiles == 0) return DAMN_OK;
+  k_spmv_sorted<PLAIN, V, I, C><<<grid, C::G * C::NT + 32, L::total(p.stages), s>>>(p);
+  DAMN_CHECK_LAUNCH("k_spmv_sorted");
   return DAMN_OK;
 }
 
@@ -122,7 +151,11 @@ int launch_cfg(const SpmvParams &p, cudaStream_t s, int *gs) {
 template <typename V, typename I>
 int launch_types(const SpmvParams &p, int shape, cudaStream_t s, int *gs) {
   using CB = std::conditional_t<sizeof(V) == 8, CfgBand64, CfgBand32>;
+  using CS = std::conditional_t<sizeof(V) == 8, CfgSorted64, CfgSorted32>;
   switch (shape) {
+    case kShapeSorted:
+      return is_plain(p) ? launch_sorted<true, V, I, CS>(p, s, gs)
+                         : launch_sorted<false, V, I, CS>(p, s, gs);
     case kShapeLong: return launch_cfg<V, I, CfgLong>(p, s, gs);
     case kShapeSlices: return launch_cfg<V, I, CfgSlices>(p, s, gs);
     case kShapeBand:

@@ -23,7 +23,8 @@ pytestmark = pytest.mark.gpu
 # plan variants: no plan; heuristic plan with x windows from off or from col;
 # each tiling pinned (x windows from off); a plan without x windows (x gathered)
 MODES = ["none", "auto", "auto_col", "rows", "rows_long", "slices", "rows_gather", "band",
-         "band_col", "band_gather", "lanes4", "lanes8", "lanes16", "lanes32"]
+         "band_col", "band_gather", "lanes4", "lanes8", "lanes16", "lanes32", "sorted",
+         "sorted_col", "sorted_gather"]
 
 
 def _t(dev, a):
@@ -48,15 +49,17 @@ class Mat:
 def _plan(D, m, mode):
     if mode == "none":
         return None
-    idx = {"auto_col": m.t_col, "band_col": m.t_col, "rows_gather": None,
-           "band_gather": None}.get(mode, m.t_off)
+    idx = {"auto_col": m.t_col, "band_col": m.t_col, "sorted_col": m.t_col, "rows_gather": None,
+           "band_gather": None, "sorted_gather": None}.get(mode, m.t_off)
     p = D.Plan(m.t_rp, len(m.col), m.ncols, m.dtype, idx=idx)
     tiling = {"rows": D.DAMN_TILING_ROWS, "rows_long": D.DAMN_TILING_ROWS_LONG,
               "slices": D.DAMN_TILING_SLICES, "rows_gather": D.DAMN_TILING_ROWS,
               "band": D.DAMN_TILING_BAND, "band_col": D.DAMN_TILING_BAND,
               "band_gather": D.DAMN_TILING_BAND, "lanes4": D.DAMN_TILING_ROWS_LANES4,
               "lanes8": D.DAMN_TILING_ROWS_LANES8, "lanes16": D.DAMN_TILING_ROWS_LANES16,
-              "lanes32": D.DAMN_TILING_ROWS_LANES32}.get(mode)
+              "lanes32": D.DAMN_TILING_ROWS_LANES32, "sorted": D.DAMN_TILING_SORTED_ROWS,
+              "sorted_col": D.DAMN_TILING_SORTED_ROWS,
+              "sorted_gather": D.DAMN_TILING_SORTED_ROWS}.get(mode)
     if tiling is not None:
         p.set_tiling(tiling)
     return p
@@ -257,8 +260,8 @@ def test_device_status_clean(D, cuda_dev):
 @pytest.mark.parametrize("h", [100, 5000])
 def test_heuristic_ragged_rows(D, cuda_dev, h):
     """Random banded rows (lengths LogNormal around 12, row efficiency about
-    0.4) get the band tiling (entry-balanced slices) whatever the band width;
-    within the bound and CSR-32 == DA-CSR-16."""
+    0.4) get the sorted-rows tiling whatever the band width; within the
+    bound and CSR-32 == DA-CSR-16."""
     rng = np.random.default_rng(21)
     n = 20000
     rp, col, val = W.random_banded(n, h, rng)
@@ -266,7 +269,7 @@ def test_heuristic_ragged_rows(D, cuda_dev, h):
     plan = D.Plan(m.t_rp, len(m.col), n, torch.float64, idx=m.t_off)
     d = plan.describe()
     assert 0.3 <= d["row_efficiency"] < 0.85
-    assert d["tiling"] == D.DAMN_TILING_BAND, d
+    assert d["tiling"] == D.DAMN_TILING_SORTED_ROWS, d
     x = W.uniform_vector(n, rng)
     got = _run(D, m, x, plan=plan)
     _bound_check(m, x, got)
@@ -295,7 +298,7 @@ def test_heuristic_uniform_rows_lanes(D, cuda_dev, lanes, length):
 
 
 @pytest.mark.parametrize("stages", [2, 3, 4, 6])
-@pytest.mark.parametrize("tiling", ["band", "rows", "lanes4", "slices"])
+@pytest.mark.parametrize("tiling", ["band", "sorted", "rows", "lanes4", "slices"])
 def test_ring_depths(D, cuda_dev, tiling, stages):
     """Every ring depth gives the same bits as the automatic depth (the
     summation order does not depend on it)."""
@@ -315,7 +318,7 @@ def test_ring_depths(D, cuda_dev, tiling, stages):
 
 @pytest.mark.parametrize("h", [300, 2000, 3500, 6000, 30000])
 def test_band_ring_and_gather(D, cuda_dev, h):
-    """Band tiling across band widths: x from the ring (narrow bands), partly
+    """Band and sorted-rows tilings across band widths: x from the ring (narrow bands), partly
     or wholly gathered (bands the 8192-slot ring cannot hold); results within
     the bound, bitwise equal for CSR-32 / DA-CSR-16 and for FP32 values
     between the two formats."""
@@ -324,17 +327,18 @@ def test_band_ring_and_gather(D, cuda_dev, h):
     rp, col, val = W.random_banded(n, h, rng)
     m = Mat(D, cuda_dev, n, n, rp, col, val)
     x = W.uniform_vector(n, rng)
-    plan = _plan(D, m, "band")
-    got = _run(D, m, x, plan=plan)
-    _bound_check(m, x, got)
-    assert np.array_equal(got, _run(D, m, x, plan=plan, fmt="csr"))
-    y0 = rng.standard_normal(n)
-    got = _run(D, m, x, y0, -0.5, 2.0, plan=plan)
-    _bound_check(m, x, got, y0, -0.5, 2.0)
     m32 = Mat(D, cuda_dev, n, n, rp, col, val, torch.float32)
-    p32 = _plan(D, m32, "band")
-    g32 = _run(D, m32, x.astype(np.float32), plan=p32)
-    assert np.array_equal(g32, _run(D, m32, x.astype(np.float32), plan=p32, fmt="csr"))
+    y0 = rng.standard_normal(n)
+    for mode in ("band", "sorted"):
+        plan = _plan(D, m, mode)
+        got = _run(D, m, x, plan=plan)
+        _bound_check(m, x, got)
+        assert np.array_equal(got, _run(D, m, x, plan=plan, fmt="csr"))
+        got = _run(D, m, x, y0, -0.5, 2.0, plan=plan)
+        _bound_check(m, x, got, y0, -0.5, 2.0)
+        p32 = _plan(D, m32, mode)
+        g32 = _run(D, m32, x.astype(np.float32), plan=p32)
+        assert np.array_equal(g32, _run(D, m32, x.astype(np.float32), plan=p32, fmt="csr"))
 
 
 def test_band_outliers_and_nonsquare(D, cuda_dev):
@@ -355,7 +359,7 @@ def test_band_outliers_and_nonsquare(D, cuda_dev):
     assert OD.fit_check(n, n, rp2, col2).fits
     m = Mat(D, cuda_dev, n, n, rp2, col2, val2)
     x = W.uniform_vector(n, rng)
-    for mode in ("band", "band_col", "band_gather"):
+    for mode in ("band", "band_col", "band_gather", "sorted", "sorted_col", "sorted_gather"):
         plan = _plan(D, m, mode)
         got = _run(D, m, x, plan=plan)
         _bound_check(m, x, got)
@@ -364,7 +368,8 @@ def test_band_outliers_and_nonsquare(D, cuda_dev):
         rpn, coln, valn = W.random_banded_rect(nr, nc, 400, rng)
         mn = Mat(D, cuda_dev, nr, nc, rpn, coln, valn)
         xn = W.uniform_vector(nc, rng)
-        plan = _plan(D, mn, "band")
-        got = _run(D, mn, xn, plan=plan)
-        _bound_check(mn, xn, got)
-        assert np.array_equal(got, _run(D, mn, xn, plan=plan, fmt="csr"))
+        for mode in ("band", "sorted"):
+            plan = _plan(D, mn, mode)
+            got = _run(D, mn, xn, plan=plan)
+            _bound_check(mn, xn, got)
+            assert np.array_equal(got, _run(D, mn, xn, plan=plan, fmt="csr"))
