@@ -159,9 +159,39 @@ def round_to_bf16(v) -> np.ndarray:
     return out
 
 
+UF8 = 2.0 ** -4        # unit roundoff of FP8 E4M3 (3 stored significand bits)
+F8_TINY_ABS = 2.0 ** -10  # largest rounding error of an E4M3 subnormal
+
+
+def round_to_e4m3(v) -> np.ndarray:
+    """Round FP64 values to the nearest FP8 E4M3 value, ties to even, in one
+    rounding step; returned as FP64.
+
+    E4M3 (the 'fn' variant: no infinities) has a sign bit, 4 exponent bits
+    with bias 7 and 3 significand bits: normal values (1 + m/8) 2^(e-7) for
+    exponent fields e = 1..15, except that e = 15 with m = 7 encodes NaN, so
+    the largest finite value is 1.75 * 2^8 = 448; subnormals m/8 * 2^-6
+    (spacing 2^-9).  The neighbours of |v| in [2^e, 2^(e+1)) are 2^(e-3)
+    apart (e clamped at -6 for the subnormal range); v / spacing rounded to
+    the nearest integer with ties to even and scaled back is exact in FP64.
+    A result beyond 448 (|v| > 464, the midpoint to the next binade's first
+    step), an infinity or a NaN becomes NaN, the format having no infinity."""
+    v = np.asarray(v, dtype=np.float64)
+    out = np.full(v.shape, np.nan)
+    fin = np.isfinite(v)
+    out[fin & (v == 0)] = v[fin & (v == 0)]
+    nz = fin & (v != 0)
+    m, ex = np.frexp(v[nz])              # v = m * 2^ex, 0.5 <= |m| < 1
+    e = np.maximum(ex - 1, -6)           # floor(log2 |v|), clamped
+    spacing = np.ldexp(1.0, e - 3)
+    r = np.rint(v[nz] / spacing) * spacing
+    out[nz] = np.where(np.abs(r) > 448.0, np.nan, r)
+    return out
+
+
 def quantize(val, dtype: str) -> np.ndarray:
     """FP64 values stored in a reduced type (round to nearest, ties to even),
-    returned in FP64.  dtype: 'f64', 'f32' or 'bf16'."""
+    returned in FP64.  dtype: 'f64', 'f32', 'bf16' or 'f8e4m3'."""
     val = np.asarray(val, dtype=np.float64)
     if dtype == "f64":
         return val.copy()
@@ -169,6 +199,8 @@ def quantize(val, dtype: str) -> np.ndarray:
         return val.astype(np.float32).astype(np.float64)
     if dtype == "bf16":
         return round_to_bf16(val)
+    if dtype == "f8e4m3":
+        return round_to_e4m3(val)
     raise ValueError(dtype)
 
 

@@ -349,3 +349,54 @@ def test_recursive_summation_error_reaches_a_quarter_of_the_bound():
     assert got[0] == 1.0
     err = abs(got[0] - ex[0])
     assert err <= bnd[0] and err >= 0.24 * bnd[0]
+
+
+def test_round_to_e4m3_by_hand():
+    """E4M3 values worked out from the format: 3 significand bits, bias 7,
+    largest finite 448, subnormal spacing 2^-9, no infinity."""
+    cases = [
+        (1.0, 1.0),
+        (1 + 2 ** -4, 1.0),                    # halfway, tie to even (down)
+        (1 + 3 * 2 ** -4, 1.25),               # halfway, tie to even (up)
+        (1 + 2 ** -4 + 2 ** -30, 1.125),       # just above halfway: one rounding
+        (-2.5, -2.5),
+        (0.1, 13 * 2 ** -7),                   # 0.1 = 1.6 * 2^-4, spacing 2^-7
+        (232.0, 224.0),                        # 14.5 steps of 16, tie to even
+        (240.0, 240.0),
+        (448.0, 448.0),                        # largest finite
+        (464.0, 448.0),                        # midpoint to 480: tie to even
+        (464.01, np.nan),                      # rounds to 480, not representable
+        (2.0 ** -6, 2.0 ** -6),                # smallest normal
+        (2.0 ** -9, 2.0 ** -9),                # smallest subnormal
+        (2.0 ** -10, 0.0),                     # half of it: tie to even (zero)
+        (3 * 2.0 ** -11, 2.0 ** -9),
+        (7 * 2.0 ** -9, 7 * 2.0 ** -9),        # largest subnormal
+        (np.inf, np.nan),
+        (-0.0, -0.0),
+    ]
+    got = S.round_to_e4m3([a for a, _ in cases])
+    want = np.array([b for _, b in cases])
+    assert np.array_equal(got, want, equal_nan=True)
+    assert np.signbit(got[-1])
+
+
+def test_round_to_e4m3_matches_torch_on_fp32_inputs():
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("torch without float8_e4m3fn")
+    rng = np.random.default_rng(8)
+    v = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-4, 3, 20000),
+                        rng.uniform(-500, 500, 2000), rng.uniform(-2 ** -6, 2 ** -6, 2000)])
+    v = v.astype(np.float32)
+    ref = torch.from_numpy(v).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(S.round_to_e4m3(v.astype(np.float64)), ref, equal_nan=True)
+
+
+def test_round_to_e4m3_error_bound():
+    """|fl(a) - a| <= max(2^-4 |a|, 2^-10) for every finite a up to 448: the
+    per-value error used for the FP8 SpMV tolerance."""
+    rng = np.random.default_rng(9)
+    a = np.concatenate([rng.standard_normal(50000) * 10.0 ** rng.integers(-5, 3, 50000),
+                        rng.uniform(-448, 448, 5000)])
+    q = S.round_to_e4m3(a)
+    assert np.all(np.abs(q - a) <= np.maximum(S.UF8 * np.abs(a), S.F8_TINY_ABS))
