@@ -28,7 +28,11 @@
  *   null pointers, alignment, dtype); damn_validate_csr() checks the arrays.
  * - dtype selects the value type: DAMN_F64 (values, x and y FP64, FP64
  *   accumulation), DAMN_F32 or DAMN_BF16 (values FP32 / BF16; x and y FP32;
- *   FP32 accumulation).  val, x, y, col and off must be 16-byte aligned
+ *   FP32 accumulation).  The SpMV entry points (CSR-32, DA-CSR-16, DA-CSR-8)
+ *   also take DAMN_F8E4M3: FP8 E4M3 values (1 sign, 4 exponent bits with
+ *   bias 7, 3 significand bits, largest finite 448, no infinity), decoded
+ *   exactly to FP32, x and y FP32, FP32 accumulation -- the float8 value
+ *   column of the traffic lattice of Section 2, Fig. 3.  val, x, y, col and off must be 16-byte aligned
  *   (torch allocations are); misaligned pointers are rejected with
  *   DAMN_ERR_INVALID_ARG.
  */
@@ -56,6 +60,7 @@ extern "C" {
 #define DAMN_F64   0
 #define DAMN_F32   1
 #define DAMN_BF16  2
+#define DAMN_F8E4M3 3  /* FP8 E4M3 values (SpMV only; x and y FP32) */
 
 #define DAMN_FMT_CSR32   0
 #define DAMN_FMT_DACSR16 1
@@ -152,9 +157,11 @@ int damn_validate_csr(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *
                       const int32_t *col, int64_t *h_bad_rows, int64_t *h_bad_cols,
                       void *workspace, size_t ws_bytes, void *stream);
 
-/* Round-to-nearest-even conversion of n values: FP64 -> FP32 or BF16 (one
- * rounding step, no double rounding through FP32), or FP32 -> BF16.  Used to
- * make the reduced-precision copy of a matrix's values. */
+/* Round-to-nearest-even conversion of n values: FP64 -> FP32, BF16 or FP8
+ * E4M3 (one rounding step, no double rounding through FP32), or FP32 -> BF16
+ * or E4M3.  E4M3 has no infinity: a value beyond 464 (rounding past the
+ * largest finite 448), an infinity or a NaN becomes NaN.  Used to make the
+ * reduced-precision copy of a matrix's values. */
 int damn_cast_values(int64_t n, const void *src, int src_dtype, void *dst, int dst_dtype,
                      void *stream);
 

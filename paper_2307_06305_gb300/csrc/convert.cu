@@ -158,6 +158,27 @@ __device__ __forceinline__ uint16_t bf16_bits_from_double(double v) {
   return static_cast<uint16_t>(sign | (eb << 7) | (q & 127u));
 }
 
+// Round-to-nearest-even narrowing to FP8 E4M3, written from the encodings:
+// |v| = m 2^e with m in [1, 2) (e read from the FP64 exponent field, clamped
+// at -6, the subnormal range of E4M3); q = |v| 2^(3-e), rounded to an
+// integer with ties to even, is |v| in units of the spacing 2^(e-3), and
+// q = 16 carries into the next binade.  |v| > 464 (rounding past the largest
+// finite 448), an infinity or a NaN give NaN: the format has no infinity.
+__device__ __forceinline__ uint8_t e4m3_bits_from_double(double v) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+  const uint8_t sign = static_cast<uint8_t>((bits >> 56) & 0x80u);
+  const double a = fabs(v);
+  if (!(a <= 464.0)) return sign | 0x7Fu;
+  if (a == 0.0) return sign;
+  int e = static_cast<int>((bits >> 52) & 0x7FFu) - 1023;  // FP64 subnormals: e = -1023
+  if (e < -6) e = -6;
+  const double scale = __longlong_as_double(static_cast<long long>(1023 + 3 - e) << 52);
+  int q = static_cast<int>(__double2ll_rn(a * scale));  // exact product, RNE
+  if (e == -6 && q < 8) return sign | static_cast<uint8_t>(q);  // subnormal or zero
+  if (q == 16) { q = 8; ++e; }
+  return sign | static_cast<uint8_t>(((e + 7) << 3) | (q - 8));
+}
+
 __global__ void k_cast(long long n, const void *src, int st, void *dst, int dt) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -165,6 +186,8 @@ __global__ void k_cast(long long n, const void *src, int st, void *dst, int dt) 
                                       : static_cast<double>(static_cast<const float *>(src)[i]);
     if (dt == DAMN_F32)
       static_cast<float *>(dst)[i] = __double2float_rn(v);
+    else if (dt == DAMN_F8E4M3)
+      static_cast<uint8_t *>(dst)[i] = e4m3_bits_from_double(v);
     else
       static_cast<uint16_t *>(dst)[i] = bf16_bits_from_double(v);
   }
@@ -262,8 +285,10 @@ extern "C" int damn_cast_values(int64_t n, const void *src, int src_dtype, void 
   if (n < 0) return set_error(DAMN_ERR_INVALID_ARG, "damn_cast_values: n < 0");
   if (n == 0) return DAMN_OK;
   if (!src || !dst) return set_error(DAMN_ERR_INVALID_ARG, "damn_cast_values: NULL pointer");
-  const bool ok = (src_dtype == DAMN_F64 && (dst_dtype == DAMN_F32 || dst_dtype == DAMN_BF16)) ||
-                  (src_dtype == DAMN_F32 && dst_dtype == DAMN_BF16);
+  const bool ok =
+      (src_dtype == DAMN_F64 &&
+       (dst_dtype == DAMN_F32 || dst_dtype == DAMN_BF16 || dst_dtype == DAMN_F8E4M3)) ||
+      (src_dtype == DAMN_F32 && (dst_dtype == DAMN_BF16 || dst_dtype == DAMN_F8E4M3));
   if (!ok) return set_error(DAMN_ERR_UNSUPPORTED, "damn_cast_values: unsupported dtype pair");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int blocks = (int)std::min<int64_t>(8LL * sm_count(), (n + 255) / 256);

@@ -197,14 +197,31 @@ __device__ __forceinline__ bool named_bar_or(int id, int nthreads, bool pred) {
 // ----------------------------------------------------------------------------
 // Value types
 // ----------------------------------------------------------------------------
+// FP8 E4M3 value (the 'fn' variant: sign, 4 exponent bits with bias 7, 3
+// significand bits, no infinity, NaN = S.1111.111), stored as its byte.
+struct f8e4m3 {
+  uint8_t b;
+};
+
 template <typename T> struct AccOf;
 template <> struct AccOf<double> { using type = double; };
 template <> struct AccOf<float> { using type = float; };
 template <> struct AccOf<__nv_bfloat16> { using type = float; };
+template <> struct AccOf<f8e4m3> { using type = float; };
 
 __device__ __forceinline__ double to_acc(double v) { return v; }
 __device__ __forceinline__ float to_acc(float v) { return v; }
 __device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+// E4M3 -> FP32, exact: the 7 magnitude bits placed at the top of an FP32
+// exponent field give 2^(e-127) (1 + m/8) for e > 0 and, as an FP32
+// subnormal, m 2^-129 for e = 0; one multiplication by 2^120 moves both to
+// the E4M3 scale (2^(e-7) (1 + m/8), m 2^-9).  Magnitude bits 0x7F are NaN.
+__device__ __forceinline__ float to_acc(f8e4m3 v) {
+  const unsigned mag = v.b & 0x7Fu;
+  float f = __uint_as_float(mag << 20) * __uint_as_float((127u + 120u) << 23);  // * 2^120
+  f = mag == 0x7Fu ? __uint_as_float(0x7FC00000u) : f;
+  return __uint_as_float(__float_as_uint(f) | (static_cast<unsigned>(v.b & 0x80u) << 24));
+}
 
 __device__ __forceinline__ double fma_acc(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_acc(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -213,6 +230,9 @@ template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ld
 template <> __device__ __forceinline__ __nv_bfloat16 ldg(const __nv_bfloat16 *p) {
   unsigned short u = __ldg(reinterpret_cast<const unsigned short *>(p));
   return __ushort_as_bfloat16(u);
+}
+template <> __device__ __forceinline__ f8e4m3 ldg(const f8e4m3 *p) {
+  return f8e4m3{__ldg(reinterpret_cast<const unsigned char *>(p))};
 }
 
 }  // namespace damn

@@ -51,6 +51,9 @@ DAMN_DECL_LAUNCH(spmv_launch_dacsr16_bf16)
 DAMN_DECL_LAUNCH(spmv_launch_dacsr8_f64)
 DAMN_DECL_LAUNCH(spmv_launch_dacsr8_f32)
 DAMN_DECL_LAUNCH(spmv_launch_dacsr8_bf16)
+DAMN_DECL_LAUNCH(spmv_launch_csr32_f8)
+DAMN_DECL_LAUNCH(spmv_launch_dacsr16_f8)
+DAMN_DECL_LAUNCH(spmv_launch_dacsr8_f8)
 #undef DAMN_DECL_LAUNCH
 namespace {
 
@@ -58,15 +61,18 @@ int launch_any(const SpmvParams &p, int dtype, int fmt, int shape, cudaStream_t 
   if (fmt == DAMN_FMT_DACSR16) {
     if (dtype == DAMN_F64) return spmv_launch_dacsr16_f64(p, shape, s, gs);
     if (dtype == DAMN_F32) return spmv_launch_dacsr16_f32(p, shape, s, gs);
+    if (dtype == DAMN_F8E4M3) return spmv_launch_dacsr16_f8(p, shape, s, gs);
     return spmv_launch_dacsr16_bf16(p, shape, s, gs);
   }
   if (fmt == DAMN_FMT_DACSR8) {
     if (dtype == DAMN_F64) return spmv_launch_dacsr8_f64(p, shape, s, gs);
     if (dtype == DAMN_F32) return spmv_launch_dacsr8_f32(p, shape, s, gs);
+    if (dtype == DAMN_F8E4M3) return spmv_launch_dacsr8_f8(p, shape, s, gs);
     return spmv_launch_dacsr8_bf16(p, shape, s, gs);
   }
   if (dtype == DAMN_F64) return spmv_launch_csr32_f64(p, shape, s, gs);
   if (dtype == DAMN_F32) return spmv_launch_csr32_f32(p, shape, s, gs);
+  if (dtype == DAMN_F8E4M3) return spmv_launch_csr32_f8(p, shape, s, gs);
   return spmv_launch_csr32_bf16(p, shape, s, gs);
 }
 
@@ -542,7 +548,7 @@ static int check_spmv_args(const char *fn, int fmt, int32_t nrows, int32_t ncols
                            const void *x, void *y, const damn_plan *plan) {
   if (nrows < 0 || ncols < 0 || nnz < 0 || nnz > INT_MAX)
     return set_error(DAMN_ERR_INVALID_ARG, "%s: bad sizes", fn);
-  if (dtype != DAMN_F64 && dtype != DAMN_F32 && dtype != DAMN_BF16)
+  if (dtype != DAMN_F64 && dtype != DAMN_F32 && dtype != DAMN_BF16 && dtype != DAMN_F8E4M3)
     return set_error(DAMN_ERR_INVALID_ARG, "%s: bad dtype %d", fn, dtype);
   if (nrows > 0 && (!rowptr || !y)) return set_error(DAMN_ERR_INVALID_ARG, "%s: NULL pointer", fn);
   if (nnz > 0 && (!idx || !val || !x)) return set_error(DAMN_ERR_INVALID_ARG, "%s: NULL pointer", fn);
@@ -761,7 +767,7 @@ extern "C" int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const
   *out = nullptr;
   if (nrows < 0 || ncols < 0 || nnz < 0 || nnz > INT_MAX || (nrows > 0 && !rowptr))
     return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_create: bad arguments");
-  if (dtype != DAMN_F64 && dtype != DAMN_F32 && dtype != DAMN_BF16)
+  if (dtype != DAMN_F64 && dtype != DAMN_F32 && dtype != DAMN_BF16 && dtype != DAMN_F8E4M3)
     return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_create: bad dtype");
   if (idx && format != DAMN_FMT_CSR32 && format != DAMN_FMT_DACSR16 && format != DAMN_FMT_DACSR8)
     return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_create: bad format");

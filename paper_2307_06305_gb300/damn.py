@@ -33,8 +33,11 @@ DAMN_TILING_ROWS_LANES4, DAMN_TILING_ROWS_LANES8 = 4, 5
 DAMN_TILING_ROWS_LANES16, DAMN_TILING_ROWS_LANES32 = 6, 7
 DAMN_TILING_SORTED_ROWS = 8
 
-_DTYPE_CODE = {torch.float64: DAMN_F64, torch.float32: DAMN_F32, torch.bfloat16: DAMN_BF16}
-_VEC_DTYPE = {DAMN_F64: torch.float64, DAMN_F32: torch.float32, DAMN_BF16: torch.float32}
+DAMN_F8E4M3 = 3
+_DTYPE_CODE = {torch.float64: DAMN_F64, torch.float32: DAMN_F32, torch.bfloat16: DAMN_BF16,
+               torch.float8_e4m3fn: DAMN_F8E4M3}
+_VEC_DTYPE = {DAMN_F64: torch.float64, DAMN_F32: torch.float32, DAMN_BF16: torch.float32,
+              DAMN_F8E4M3: torch.float32}
 
 
 class DamnError(RuntimeError):

@@ -123,3 +123,21 @@ def test_cast_values(D, cuda_dev):
     assert np.array_equal(f32, OS.quantize(v, "f32"))
     bf = D.damn_cast_values(t, torch.bfloat16).double().cpu().numpy()
     assert np.array_equal(bf, OS.quantize(v, "bf16"))
+    # FP8 E4M3 (one rounding step from FP64; beyond 464, inf and NaN -> NaN)
+    v8 = np.concatenate([v, rng.uniform(-500, 500, 20000), rng.uniform(-2 ** -5, 2 ** -5, 20000),
+                         [1 + 2 ** -4 + 2 ** -30, 464.0, 464.01, 448.0, 2.0 ** -10,
+                          3 * 2.0 ** -11, np.inf, -np.inf, np.nan, 1e-310]])
+    t8 = torch.from_numpy(v8).to(cuda_dev)
+    f8 = D.damn_cast_values(t8, torch.float8_e4m3fn)
+    assert np.array_equal(f8.double().cpu().numpy(), OS.quantize(v8, "f8e4m3"), equal_nan=True)
+    # the NaN encoding is the format's (S.1111.111), and signed zeros keep their sign
+    bits = f8.view(torch.uint8).cpu().numpy()
+    assert set(bits[np.isnan(OS.quantize(v8, "f8e4m3"))]) <= {0x7F, 0xFF}
+    z = D.damn_cast_values(torch.tensor([-0.0, 0.0, -1e-300], dtype=torch.float64, device=cuda_dev),
+                           torch.float8_e4m3fn).view(torch.uint8).cpu().tolist()
+    assert z == [0x80, 0x00, 0x80]
+    # FP32 -> E4M3 equals torch's own conversion of FP32 values
+    v32 = v8[np.isfinite(v8)].astype(np.float32)
+    g32 = D.damn_cast_values(torch.from_numpy(v32).to(cuda_dev), torch.float8_e4m3fn)
+    ref32 = torch.from_numpy(v32).to(torch.float8_e4m3fn)
+    assert np.array_equal(g32.double().cpu().numpy(), ref32.double().numpy(), equal_nan=True)

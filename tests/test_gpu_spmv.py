@@ -41,8 +41,8 @@ class Mat:
         self.t_rp = _t(dev, rp)
         self.t_col = _t(dev, col)
         self.t_off = _t(dev, self.off.astype(np.int16))
-        self.t_val = _t(dev, val).to(dtype) if dtype != torch.bfloat16 else \
-            D.damn_cast_values(_t(dev, val), torch.bfloat16)
+        self.t_val = _t(dev, val).to(dtype) if dtype in (torch.float64, torch.float32) else \
+            D.damn_cast_values(_t(dev, val), dtype)
         self.dtype = dtype
 
 
@@ -96,6 +96,10 @@ def test_config1_dyadic_bitwise(D, cuda_dev, mode):
     mb = Mat(D, cuda_dev, n, n, rp, col, val, torch.bfloat16)
     planb = _plan(D, mb, mode)
     assert np.array_equal(_run(D, mb, x, plan=planb), ref)
+    # and with FP8 E4M3 values (4 and -1 are exact in E4M3)
+    m8 = Mat(D, cuda_dev, n, n, rp, col, val, torch.float8_e4m3fn)
+    plan8 = _plan(D, m8, mode)
+    assert np.array_equal(_run(D, m8, x, plan=plan8), ref)
 
 
 def _bound_check(m, x, got, y0=None, alpha=1.0, beta=0.0, u=OS.U64, vals=None):
@@ -185,7 +189,10 @@ def test_nonsquare(D, cuda_dev, shape):
         assert np.array_equal(got, _run(D, m, x, plan=plan, fmt="csr"))
 
 
-@pytest.mark.parametrize("lowp", [torch.float32, torch.bfloat16])
+LOWP = {torch.float32: "f32", torch.bfloat16: "bf16", torch.float8_e4m3fn: "f8e4m3"}
+
+
+@pytest.mark.parametrize("lowp", list(LOWP))
 @pytest.mark.parametrize("mode", MODES)
 def test_reduced_precision(D, cuda_dev, lowp, mode):
     rng = np.random.default_rng(31)
@@ -193,15 +200,21 @@ def test_reduced_precision(D, cuda_dev, lowp, mode):
     rp, col, val = W.random_banded(n, 500, rng)
     m = Mat(D, cuda_dev, n, n, rp, col, val, lowp)
     x32 = W.uniform_vector(n, rng).astype(np.float32)
-    vq = OS.quantize(val, "f32" if lowp == torch.float32 else "bf16")
+    vq = OS.quantize(val, LOWP[lowp])
     plan = _plan(D, m, mode)
     got = _run(D, m, x32.astype(np.float64), plan=plan)
     _bound_check(m, x32.astype(np.float64), got, u=OS.U32, vals=vq)
     assert np.array_equal(got, _run(D, m, x32.astype(np.float64), plan=plan, fmt="csr"))
-    # error against the FP64 matrix, stated per dtype
-    u_v = OS.U32 if lowp == torch.float32 else OS.UBF16
+    # error against the FP64 matrix, stated per dtype: the value rounding
+    # (relative u_v; E4M3 subnormals absolute 2^-10) plus the FP32 sums
     ex64 = OS.spmv_exact(n, rp, m.off, val, x32.astype(np.float64))
-    tot = OS.error_bound(n, rp, m.off, vq, x32, u=OS.U32) + u_v * OS.abs_row_sums(n, rp, m.off, val, x32)
+    tot = OS.error_bound(n, rp, m.off, vq, x32, u=OS.U32)
+    if lowp == torch.float8_e4m3fn:
+        tot = tot + OS.UF8 * OS.abs_row_sums(n, rp, m.off, val, x32) + \
+            OS.F8_TINY_ABS * OS.abs_row_sums(n, rp, m.off, np.ones_like(val), x32)
+    else:
+        u_v = OS.U32 if lowp == torch.float32 else OS.UBF16
+        tot = tot + u_v * OS.abs_row_sums(n, rp, m.off, val, x32)
     assert np.all(np.abs(got - ex64) <= tot)
 
 
