@@ -219,14 +219,14 @@ def run_reference(args, rank, world):
 
 
 PROFILE_CASES = ("stencil27_160_rows_long", "batch512_f64_k1", "laplace3d_128",
-                 "banded_<n>_h<h>_<tiling>_<fmt>")
+                 "laplace3d_128_values", "banded_<n>_h<h>_<tiling>_<fmt>")
 
 
 def profile_case(name):
     """argparse type of --case: a fixed case name, or a random banded case
     banded_<n>_h<h>_<tiling>_<fmt> (n like 1e6, tiling auto / rows /
     rows_long / slices, fmt da16 / csr32)."""
-    if name in PROFILE_CASES[:3]:
+    if name in PROFILE_CASES[:4]:
         return name
     parts = name.split("_")
     tiling = "_".join(parts[3:-1])
@@ -271,6 +271,22 @@ def run_case(args):
                 D.damn_spmv_dacsr16(t_rp, off, t_val, x, y, plan=plan)
             else:
                 D.damn_spmv_csr32(t_rp, t_col, t_val, x, y, plan=plan)
+    elif args.case == "laplace3d_128_values":
+        rp, col, val, xh = build_inputs()
+        n, nnz = len(rp) - 1, len(col)
+        t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
+        off, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
+        t_val = torch.from_numpy(val).to(dev)
+        x = torch.from_numpy(xh).to(dev)
+        runs = []
+        for dt in (torch.float64, torch.float32, torch.bfloat16, torch.float8_e4m3fn):
+            v = t_val if dt == torch.float64 else D.damn_cast_values(t_val, dt)
+            xv = x if dt == torch.float64 else x.float()
+            y = torch.empty(n, dtype=xv.dtype, device=dev)
+            runs.append((v, xv, y, D.Plan(t_rp, nnz, n, dt, idx=off)))
+        for _ in range(args.steps):
+            for v, xv, y, pl in runs:
+                D.damn_spmv_dacsr16(t_rp, off, v, xv, y, plan=pl)
     elif args.case == "laplace3d_128":
         rp, col, val, xh = build_inputs()
         n, nnz = len(rp) - 1, len(col)
@@ -655,7 +671,7 @@ BANDED_POINTS_FULL = tuple((n, h) for n in (100_000, 300_000, 1_000_000, 3_000_0
                                             20_000_000) for h in (100, 1000, 30000))
 L2_BYTES = 126e6
 TILING_NAMES = ("slices", "rows", "rows_long", "band", "lanes4", "lanes8", "lanes16",
-                "lanes32", "sorted")   # DAMN_TILING_* 0 .. 8
+                "lanes32", "sorted", "rows_x2")   # DAMN_TILING_* 0 .. 9
 BANDED_TILINGS = (0, 2, 3, 8)  # the tilings timed in the banded section
 
 
@@ -765,9 +781,11 @@ def main():
                             "small",
                     help="comma list of secondary sections to run after the headline ('' for none)")
     ap.add_argument("--section-reps", type=int, default=10)
+    ap.add_argument("--step-reps", type=int, default=30,
+                    help="individually timed steps (event pair each) after the window, >= 30")
     ap.add_argument("--e2e-parts", type=int, default=1,
                     help="parts (streams) each end-to-end upload / download is split into")
-    ap.add_argument("--tiling", default="auto", choices=["auto", "rows", "rows_long", "slices"],
+    ap.add_argument("--tiling", default="auto", choices=["auto"] + list(TILING_NAMES),
                     help="headline plan tiling: autotuned, or fixed")
     ap.add_argument("--case", default=None, type=profile_case,
                     help="run only the launches of one profiled kernel (for ncu), no timing")
@@ -810,11 +828,12 @@ def main():
         plans[0].autotune(D.DAMN_FMT_DACSR16, t_off[0], t_val[0], t_x, y)
         tiling = plans[0].describe()["tiling"]
     else:
-        tiling = {"rows": D.DAMN_TILING_ROWS, "rows_long": D.DAMN_TILING_ROWS_LONG,
-                  "slices": D.DAMN_TILING_SLICES}[args.tiling]
+        tiling = TILING_NAMES.index(args.tiling)
         plans[0].set_tiling(tiling)
+    stages = plans[0].describe()["stages_requested"]
     for c in range(1, NCOPY):
         plans[c].set_tiling(tiling)
+        plans[c].set_stages(stages)
     stream = torch.cuda.current_stream()
 
     def step_da(i):
@@ -848,9 +867,28 @@ def main():
             t = float(tt.item())
         return t
 
+    def per_step(fn, reps):
+        """Each of `reps` steps bracketed by its own event pair on the
+        launching stream (median / min / max in us), after the window."""
+        ts = []
+        for i in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(i)
+            e1.record(stream)
+            ts.append((e0, e1))
+        torch.cuda.synchronize()
+        us = sorted(a.elapsed_time(b) * 1e3 for a, b in ts)
+        return {"reps": reps, "median_us": round(statistics.median(us), 3),
+                "min_us": round(us[0], 3), "max_us": round(us[-1], 3)}
+
     clk = ClockSampler(local).__enter__()  # sampled across every timed phase below
     t_da = timed(step_da, args.steps, args.warmup)
     t_cs = timed(step_csr, args.steps, args.warmup)
+    reps = max(30, args.step_reps)
+    steps_da = per_step(step_da, reps)
+    steps_cs = per_step(step_csr, reps)
     if D.damn_device_status() != 0:
         raise RuntimeError("device status word reports a timed-out wait")
 
@@ -862,11 +900,17 @@ def main():
 
     # reduced-precision values (FP32 / BF16 values, FP32 vectors)
     mixed = {}
-    for name, dt, vb in (("f32", torch.float32, 4), ("bf16", torch.bfloat16, 2)):
+    for name, dt, vb in (("f32", torch.float32, 4), ("bf16", torch.bfloat16, 2),
+                         ("f8e4m3", torch.float8_e4m3fn, 1)):
         vals = [D.damn_cast_values(t_val[c], dt) for c in range(NCOPY)]
         x32 = t_x.float()
         y32 = torch.empty(n, dtype=torch.float32, device=dev)
         pl = [D.Plan(t_rp[c], nnz, n, dt, idx=t_off[c]) for c in range(NCOPY)]
+        pl[0].autotune(D.DAMN_FMT_DACSR16, t_off[0], vals[0], x32, y32)
+        dsc = pl[0].describe()
+        for c in range(1, NCOPY):
+            pl[c].set_tiling(dsc["tiling"])
+            pl[c].set_stages(dsc["stages_requested"])
 
         def step_m(i, vals=vals, pl=pl, x32=x32, y32=y32):
             c = i % NCOPY
@@ -879,6 +923,8 @@ def main():
         bm = spmv_bytes(n, nnz, 2, vb, 4)
         bc = spmv_bytes(n, nnz, 4, vb, 4)
         mixed[name] = {"gbs": round(bm / tm / 1e9, 1), "us": round(tm * 1e6, 2),
+                       "frac_hbm": round(bm / tm / 1e9 / float(measured_peaks()[0]["hbm_gbs"]), 4),
+                       "tiling": TILING_NAMES[dsc["tiling"]], "stages": dsc["stages"],
                        "bytes": bm, "csr32_us": round(tc * 1e6, 2),
                        "csr32_gbs": round(bc / tc / 1e9, 1),
                        "speedup_da16_over_csr32": round(tc / tm, 4),
@@ -972,6 +1018,11 @@ def main():
                      "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
                      "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                      "algorithmic_bytes_per_launch": b_da,
+                     "da16_us": round(per_step_da * 1e6, 3),
+                     "csr32_us": round(per_step_cs * 1e6, 3),
+                     "speedup_da16_over_csr32": round(per_step_cs / per_step_da, 4),
+                     "model_speedup": round(b_cs / b_da, 4),
+                     "per_step_da16": steps_da, "per_step_csr32": steps_cs,
                      # the second bound of FP64 SpMV on this part: one FMA per entry
                      "fp64": {"achieved_tfma_per_s": round(nnz / per_step_da / 1e12, 4),
                               "peak_tfma_per_s": FP64_TFMA_NOMINAL,
@@ -990,6 +1041,8 @@ def main():
                 "pipelined": f"upload / SpMV / download of consecutive steps overlap; each copy "
                              f"split into {args.e2e_parts} parts on their own streams"},
         "gpu_launches": args.steps,
+        "timing": f"one CUDA-event window over the {args.steps} steps (value, ms_per_step); "
+                  f"then {reps} steps each timed by its own event pair (roofline.per_step_*)",
         "clocks": clk.summary(),
     }
     secs = [t for t in args.sections.split(",") if t]

@@ -245,6 +245,7 @@ typedef struct {
 #define DAMN_TILING_ROWS_LANES16  6
 #define DAMN_TILING_ROWS_LANES32  7
 #define DAMN_TILING_SORTED_ROWS   8
+#define DAMN_TILING_ROWS_X2       9
 
 /* Builds a plan for one matrix and value dtype: the partition of the rows
  * into tiles and the compute mode (the tiling), chosen from the row-length
@@ -269,8 +270,9 @@ int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *r
                      int format, const void *idx, int dtype, void *stream, damn_plan **out);
 
 /* Autotuner: times every tiling on the given operands (format DAMN_FMT_*;
- * idx is col or off) -- rows with 1 and 2 lanes per row, balanced slices,
- * band, and rows with 4 / 8 / 16 / 32 lanes per row where an average row has
+ * idx is col or off) -- rows with 1 and 2 lanes per row, rows with twice
+ * the rows per thread, balanced slices, band, sorted rows, and rows with
+ * 4 / 8 / 16 / 32 lanes per row where an average row has
  * at least two entries per lane -- keeps the fastest, then times ring depths
  * of 2 to 6 stages for it and keeps one only when it is at least 3 % faster
  * than the automatic depth.  y is overwritten.  Synchronises stream. */
@@ -280,6 +282,9 @@ int damn_plan_autotune(damn_plan *plan, int format, const void *idx, const void 
 /* Pins the plan's tiling:
  *  DAMN_TILING_ROWS: tiles of 256 rows with FP64 values, one row per
  *    thread, or 512 rows with FP32 / BF16 values, two rows per thread;
+ *  DAMN_TILING_ROWS_X2: as DAMN_TILING_ROWS with twice the rows per thread
+ *    (FP64 values: 512-row tiles, two rows per thread; FP32 / BF16 / FP8
+ *    values: 1024-row tiles, four rows per thread);
  *  DAMN_TILING_ROWS_LONG: 128-row tiles, two lanes per row;
  *  DAMN_TILING_ROWS_LANES4 / 8 / 16 / 32: tiles of 64 / 32 / 16 / 8 rows,
  *    4 / 8 / 16 / 32 lanes per row (lane i takes entries i, i + E, ...; the

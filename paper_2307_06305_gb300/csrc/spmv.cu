@@ -30,7 +30,9 @@ constexpr int kXGap = 32;           // columns: smaller gaps are staged, not spl
 static_assert(kBalancedItems / kRowWeight <= CfgSlices::CAP_ROWS, "balanced tiles too tall");
 static_assert(CfgShort::TILE_ROWS <= CfgShort::CAP_ROWS &&
                   CfgShortNarrow::TILE_ROWS <= CfgShortNarrow::CAP_ROWS &&
-                  CfgLong::TILE_ROWS <= CfgLong::CAP_ROWS && 256 <= CfgSlices::CAP_ROWS,
+                  CfgLong::TILE_ROWS <= CfgLong::CAP_ROWS && 256 <= CfgSlices::CAP_ROWS &&
+                  CfgShortX2::TILE_ROWS <= CfgShortX2::CAP_ROWS &&
+                  CfgShortNarrowX2::TILE_ROWS <= CfgShortNarrowX2::CAP_ROWS,
               "row tiles too tall");
 static_assert(kBalancedItems <= CfgBand64::CAP_NZ && kBalancedItems / kRowWeight <= CfgBand64::CAP_ROWS &&
                   kBalancedItems <= CfgBand32::CAP_NZ &&
@@ -129,8 +131,10 @@ __global__ void k_plan_stats(int nrows, const int *__restrict__ rowptr, int tile
   }
 }
 
-constexpr int kXSortCap = 4096;  // >= every CAP_NZ
-constexpr int kXRowsCap = 513;   // >= every CAP_ROWS + 1
+constexpr int kXSortCap = 8192;  // >= every CAP_NZ
+constexpr int kXRowsCap = 1025;  // >= every CAP_ROWS + 1
+static_assert(CfgShortNarrowX2::CAP_NZ <= kXSortCap && CfgShortNarrowX2::CAP_ROWS + 1 <= kXRowsCap,
+              "x-window plan kernel too small for a stage");
 constexpr int kXStartCap = 64;   // segment starts considered for merging
 
 // x window of every tile: columns of the tile's entries, sorted (bitonic, in
@@ -421,6 +425,10 @@ static CfgGeom cfg_geom(int shape, int dtype) {
     case kShapeLanes8: return {CfgLanes8::TILE_ROWS, CfgLanes8::CAP_NZ, CfgLanes8::XCAP, 256};
     case kShapeLanes16: return {CfgLanes16::TILE_ROWS, CfgLanes16::CAP_NZ, CfgLanes16::XCAP, 256};
     case kShapeLanes32: return {CfgLanes32::TILE_ROWS, CfgLanes32::CAP_NZ, CfgLanes32::XCAP, 256};
+    case kShapeShortX2:
+      if (dtype != DAMN_F64)
+        return {CfgShortNarrowX2::TILE_ROWS, CfgShortNarrowX2::CAP_NZ, CfgShortNarrowX2::XCAP, 256};
+      return {CfgShortX2::TILE_ROWS, CfgShortX2::CAP_NZ, CfgShortX2::XCAP, 256};
     case kShapeSorted:
       return {CfgSorted64::NT, CfgSorted64::CAP_NZ,
               dtype == DAMN_F64 ? CfgSorted64::W : CfgSorted32::W,
@@ -444,6 +452,7 @@ static int shape_of_tiling(int tiling) {
     case DAMN_TILING_ROWS_LANES16: return kShapeLanes16;
     case DAMN_TILING_ROWS_LANES32: return kShapeLanes32;
     case DAMN_TILING_SORTED_ROWS: return kShapeSorted;
+    case DAMN_TILING_ROWS_X2: return kShapeShortX2;
     default: return -1;
   }
 }
@@ -457,6 +466,7 @@ static int tiling_of_shape(int shape) {
     case kShapeLanes16: return DAMN_TILING_ROWS_LANES16;
     case kShapeLanes32: return DAMN_TILING_ROWS_LANES32;
     case kShapeSorted: return DAMN_TILING_SORTED_ROWS;
+    case kShapeShortX2: return DAMN_TILING_ROWS_X2;
     default: return DAMN_TILING_ROWS;
   }
 }
@@ -860,8 +870,9 @@ extern "C" int damn_plan_autotune(damn_plan *plan, int format, const void *idx, 
   // 1. tilings: the fixed shapes, and the lanes-per-row tilings whose lanes
   //    would each hold at least two entries of an average row
   const double mean = (double)plan->nnz / plan->nrows;
-  int cands[9], nc = 0;
+  int cands[10], nc = 0;
   cands[nc++] = DAMN_TILING_ROWS;
+  cands[nc++] = DAMN_TILING_ROWS_X2;
   cands[nc++] = DAMN_TILING_ROWS_LONG;
   cands[nc++] = DAMN_TILING_SLICES;
   cands[nc++] = DAMN_TILING_BAND;

@@ -159,6 +159,11 @@ using CfgShort = KCfg<256, 1792, 256, 1280, 3, 1>;
 using CfgShortNarrow = KCfg<256, 3584, 512, 2560, 3, 2>;
 using CfgLong = KCfg<256, 3584, 128, 1536, 2, 1, 2>;
 using CfgSlices = KCfg<256, 2048, 512, 1280, 2, 1>;
+// Rows mode with twice the rows per thread of CfgShort / CfgShortNarrow:
+// FP64 values two rows per thread (two independent FMA chains), FP32 / BF16
+// / FP8 values four; tiles of 512 / 1024 rows, two CTAs per SM.
+using CfgShortX2 = KCfg<256, 3584, 512, 2048, 2, 2>;
+using CfgShortNarrowX2 = KCfg<256, 7168, 1024, 4096, 2, 4>;
 using CfgLanes4 = KCfg<256, 3584, 64, 1536, 2, 1, 4>;
 using CfgLanes8 = KCfg<256, 3584, 32, 1536, 2, 1, 8>;
 using CfgLanes16 = KCfg<256, 3584, 16, 1536, 2, 1, 16>;
@@ -175,6 +180,7 @@ enum Shape {
   kShapeLanes16 = 6,
   kShapeLanes32 = 7,
   kShapeSorted = 8,  // row tiles sorted by length, one row per thread, x ring
+  kShapeShortX2 = 9, // rows, one lane per row, twice the rows per thread of kShapeShort
 };
 
 constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

@@ -161,6 +161,11 @@ int launch_types(const SpmvParams &p, int shape, cudaStream_t s, int *gs) {
     case kShapeBand:
       return is_plain(p) ? launch_band<true, V, I, CB>(p, s, gs)
                          : launch_band<false, V, I, CB>(p, s, gs);
+    case kShapeShortX2:
+      if constexpr (sizeof(V) < 8)
+        return launch_cfg<V, I, CfgShortNarrowX2>(p, s, gs);
+      else
+        return launch_cfg<V, I, CfgShortX2>(p, s, gs);
     case kShapeLanes4: return launch_cfg<V, I, CfgLanes4>(p, s, gs);
     case kShapeLanes8: return launch_cfg<V, I, CfgLanes8>(p, s, gs);
     case kShapeLanes16: return launch_cfg<V, I, CfgLanes16>(p, s, gs);

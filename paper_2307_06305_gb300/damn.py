@@ -31,7 +31,7 @@ DAMN_FMT_CSR32, DAMN_FMT_DACSR16, DAMN_FMT_DACSR8 = 0, 1, 2
 DAMN_TILING_SLICES, DAMN_TILING_ROWS, DAMN_TILING_ROWS_LONG, DAMN_TILING_BAND = 0, 1, 2, 3
 DAMN_TILING_ROWS_LANES4, DAMN_TILING_ROWS_LANES8 = 4, 5
 DAMN_TILING_ROWS_LANES16, DAMN_TILING_ROWS_LANES32 = 6, 7
-DAMN_TILING_SORTED_ROWS = 8
+DAMN_TILING_SORTED_ROWS, DAMN_TILING_ROWS_X2 = 8, 9
 
 DAMN_F8E4M3 = 3
 _DTYPE_CODE = {torch.float64: DAMN_F64, torch.float32: DAMN_F32, torch.bfloat16: DAMN_BF16,

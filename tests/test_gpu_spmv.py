@@ -24,7 +24,7 @@ pytestmark = pytest.mark.gpu
 # each tiling pinned (x windows from off); a plan without x windows (x gathered)
 MODES = ["none", "auto", "auto_col", "rows", "rows_long", "slices", "rows_gather", "band",
          "band_col", "band_gather", "lanes4", "lanes8", "lanes16", "lanes32", "sorted",
-         "sorted_col", "sorted_gather"]
+         "sorted_col", "sorted_gather", "rows_x2"]
 
 
 def _t(dev, a):
@@ -59,7 +59,8 @@ def _plan(D, m, mode):
               "lanes8": D.DAMN_TILING_ROWS_LANES8, "lanes16": D.DAMN_TILING_ROWS_LANES16,
               "lanes32": D.DAMN_TILING_ROWS_LANES32, "sorted": D.DAMN_TILING_SORTED_ROWS,
               "sorted_col": D.DAMN_TILING_SORTED_ROWS,
-              "sorted_gather": D.DAMN_TILING_SORTED_ROWS}.get(mode)
+              "sorted_gather": D.DAMN_TILING_SORTED_ROWS,
+              "rows_x2": D.DAMN_TILING_ROWS_X2}.get(mode)
     if tiling is not None:
         p.set_tiling(tiling)
     return p
@@ -311,7 +312,7 @@ def test_heuristic_uniform_rows_lanes(D, cuda_dev, lanes, length):
 
 
 @pytest.mark.parametrize("stages", [2, 3, 4, 6])
-@pytest.mark.parametrize("tiling", ["band", "sorted", "rows", "lanes4", "slices"])
+@pytest.mark.parametrize("tiling", ["band", "sorted", "rows", "rows_x2", "lanes4", "slices"])
 def test_ring_depths(D, cuda_dev, tiling, stages):
     """Every ring depth gives the same bits as the automatic depth (the
     summation order does not depend on it)."""
