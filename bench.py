@@ -90,7 +90,7 @@ def kernel_source_hash():
     removed (a comment edit does not invalidate recorded counters)."""
     import re
     h = hashlib.sha256()
-    for name in ("spmv_kernel.cuh", "spmv.cu", "damn_common.cuh"):
+    for name in ("spmv_kernel.cuh", "spmv_launch.cuh", "spmv.cu", "damn_common.cuh"):
         with open(os.path.join(ROOT, "paper_2307_06305_gb300", "csrc", name)) as f:
             text = f.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
