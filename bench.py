@@ -219,14 +219,15 @@ def run_reference(args, rank, world):
 
 
 PROFILE_CASES = ("stencil27_160_rows_long", "batch512_f64_k1", "laplace3d_128",
-                 "laplace3d_128_values", "banded_<n>_h<h>_<tiling>_<fmt>")
+                 "laplace3d_128_values", "cg_160_f64", "cg_ir_160_f32", "cg_ir_160_bf16",
+                 "banded_<n>_h<h>_<tiling>_<fmt>")
 
 
 def profile_case(name):
     """argparse type of --case: a fixed case name, or a random banded case
     banded_<n>_h<h>_<tiling>_<fmt> (n like 1e6, tiling auto / rows /
     rows_long / slices, fmt da16 / csr32)."""
-    if name in PROFILE_CASES[:4]:
+    if name in PROFILE_CASES[:7]:
         return name
     parts = name.split("_")
     tiling = "_".join(parts[3:-1])
@@ -271,6 +272,28 @@ def run_case(args):
                 D.damn_spmv_dacsr16(t_rp, off, t_val, x, y, plan=plan)
             else:
                 D.damn_spmv_csr32(t_rp, t_col, t_val, x, y, plan=plan)
+    elif args.case in ("cg_160_f64", "cg_ir_160_f32", "cg_ir_160_bf16"):
+        rp, col, val = W.stencil27(160)
+        n, nnz = len(rp) - 1, len(col)
+        t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
+        off, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
+        t_val = torch.from_numpy(val).to(dev)
+        xs = torch.from_numpy(W.uniform_vector(n, W.rng_for(4, 1))).to(dev)
+        b = torch.empty(n, dtype=torch.float64, device=dev)
+        D.damn_spmv_dacsr16(t_rp, off, t_val, xs, b)
+        p64 = D.Plan(t_rp, nnz, n, torch.float64, idx=off)
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        for _ in range(args.steps):
+            x.zero_()
+            if args.case == "cg_160_f64":
+                D.damn_cg(t_rp, off, t_val, b, x, 1e-10, 2000, plan=p64)
+            else:
+                lowp = torch.float32 if args.case.endswith("f32") else torch.bfloat16
+                vl = D.damn_cast_values(t_val, lowp)
+                pl = D.Plan(t_rp, nnz, n, lowp, idx=off)
+                D.damn_cg_ir(t_rp, off, t_val, vl, b, x, 1e-10,
+                             1e-3 if lowp == torch.float32 else 1e-2, 200, 60,
+                             plan64=p64, plan_low=pl)
     elif args.case == "laplace3d_128_values":
         rp, col, val, xh = build_inputs()
         n, nnz = len(rp) - 1, len(col)

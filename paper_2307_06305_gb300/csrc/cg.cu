@@ -63,11 +63,53 @@ __device__ double block_sum(const double *part, int n, double *red) {
 template <typename T>
 __device__ __forceinline__ double to_d(T v) { return static_cast<double>(v); }
 
-// a = rr / (p.q); x += a p; r -= a q; partial r.r -> part_rr[blockIdx]
+// 16 bytes of a vector: 4 floats or 2 doubles per load.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  using type = float4;
+  static constexpr int N = 4;
+  __device__ static float get(const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+  __device__ static void set(float4 &v, int i, float f) {
+    if (i == 0) v.x = f; else if (i == 1) v.y = f; else if (i == 2) v.z = f; else v.w = f;
+  }
+};
+template <> struct Vec16<double> {
+  using type = double2;
+  static constexpr int N = 2;
+  __device__ static double get(const double2 &v, int i) { return i == 0 ? v.x : v.y; }
+  __device__ static void set(double2 &v, int i, double f) { if (i == 0) v.x = f; else v.y = f; }
+};
+
+__device__ __forceinline__ bool all_aligned16(const void *a, const void *b, const void *c,
+                                              const void *d) {
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
+           reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(d)) & 15u) == 0;
+}
+
+// Per-CTA sum of the threads' dot accumulators into part[blockIdx.x].
+template <typename T>
+__device__ __forceinline__ void block_partial(const DotAcc<T> &acc, double *red, double *part) {
+  double s = acc.value();
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    part[blockIdx.x] = t;
+  }
+}
+
+// a = rr / (p.q); x += a p; r -= a q; partial r.r -> part_rr[blockIdx].
+// 16-byte loads when every vector is 16-byte aligned (the tail and
+// misaligned vectors element by element).
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
 k_cg_update(int n, const double *part_pq, int npq, CgScalars *sc, int parity, T *x, T *r,
             const T *p, const T *q, double *part_rr) {
+  using VT = Vec16<T>;
+  using V = typename VT::type;
   __shared__ double red[kVecThreads / 32];
   if (sc->done) return;
   const double pq = block_sum(part_pq, npq, red);
@@ -79,23 +121,34 @@ k_cg_update(int n, const double *part_pq, int npq, CgScalars *sc, int parity, T 
     return;
   }
   const T at = static_cast<T>(a);
-  double s = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  DotAcc<T> acc;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long head = 0;
+  if (all_aligned16(x, r, p, q)) {
+    const long long nv = n / VT::N;
+    head = nv * VT::N;
+    for (long long v = tid; v < nv; v += stride) {
+      V xv = reinterpret_cast<const V *>(x)[v], rv = reinterpret_cast<const V *>(r)[v];
+      const V pv = reinterpret_cast<const V *>(p)[v], qv = reinterpret_cast<const V *>(q)[v];
+#pragma unroll
+      for (int k = 0; k < VT::N; ++k) {
+        VT::set(xv, k, VT::get(xv, k) + at * VT::get(pv, k));
+        const T ri = VT::get(rv, k) - at * VT::get(qv, k);
+        VT::set(rv, k, ri);
+        acc.add(ri, ri);
+      }
+      reinterpret_cast<V *>(x)[v] = xv;
+      reinterpret_cast<V *>(r)[v] = rv;
+    }
+  }
+  for (long long i = head + tid; i < n; i += stride) {
     x[i] = x[i] + at * p[i];
     const T ri = r[i] - at * q[i];
     r[i] = ri;
-    s = __fma_rn(to_d(ri), to_d(ri), s);
+    acc.add(ri, ri);
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < kVecThreads / 32; ++i) t += red[i];
-    part_rr[blockIdx.x] = t;
-  }
+  block_partial<T>(acc, red, part_rr);
 }
 
 // rr' = sum part_rr; b = rr'/rr; p = r + b p; flags convergence
@@ -103,14 +156,28 @@ template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
 k_cg_direction(int n, const double *part_rr, int nrr, CgScalars *sc, int parity, const T *r,
                T *p) {
+  using VT = Vec16<T>;
+  using V = typename VT::type;
   __shared__ double red[kVecThreads / 32];
   if (sc->done) return;
   const double rr_new = block_sum(part_rr, nrr, red);
   const double beta = rr_new / sc->rr[parity];
   const T bt = static_cast<T>(beta);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    p[i] = r[i] + bt * p[i];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long head = 0;
+  if (all_aligned16(r, p, r, p)) {
+    const long long nv = n / VT::N;
+    head = nv * VT::N;
+    for (long long v = tid; v < nv; v += stride) {
+      const V rv = reinterpret_cast<const V *>(r)[v];
+      V pv = reinterpret_cast<const V *>(p)[v];
+#pragma unroll
+      for (int k = 0; k < VT::N; ++k) VT::set(pv, k, VT::get(rv, k) + bt * VT::get(pv, k));
+      reinterpret_cast<V *>(p)[v] = pv;
+    }
+  }
+  for (long long i = head + tid; i < n; i += stride) p[i] = r[i] + bt * p[i];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     sc->rr[parity ^ 1] = rr_new;
     sc->iters += 1;
@@ -119,7 +186,8 @@ k_cg_direction(int n, const double *part_rr, int nrr, CgScalars *sc, int parity,
   }
 }
 
-// Starts a CG run: p = r, rr = sum part (r.r), done = (rr <= tol2)
+// Starts a CG run: p = r, rr = sum part (r.r), done = (rr <= tol2); a
+// negative tol2_rel asks for tol2 = -tol2_rel * rr (relative to the start)
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
 k_cg_start(int n, const double *part, int npart, CgScalars *sc, double tol2_rel, int max_iter,
@@ -130,6 +198,8 @@ k_cg_start(int n, const double *part, int npart, CgScalars *sc, double tol2_rel,
        i += (long long)gridDim.x * blockDim.x)
     p[i] = r[i];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // tol2_rel < 0: the tolerance is relative to the start, -tol2_rel * rr
+    if (tol2_rel < 0.0) tol2_rel = -tol2_rel * rr;
     sc->rr[0] = rr;
     sc->rr[1] = rr;
     sc->tol2 = tol2_rel;
@@ -139,23 +209,17 @@ k_cg_start(int n, const double *part, int npart, CgScalars *sc, double tol2_rel,
   }
 }
 
-// Partial sums of v.v (FP64 accumulation of exact products).
+// Partial sums of v.v (DotAcc: FP64 for FP64 vectors, compensated FP32 of
+// exact products for FP32 vectors).
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
 k_dot_self(int n, const T *v, double *part) {
   __shared__ double red[kVecThreads / 32];
-  double s = 0.0;
+  DotAcc<T> acc;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    s = __fma_rn(to_d(v[i]), to_d(v[i]), s);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < kVecThreads / 32; ++i) t += red[i];
-    part[blockIdx.x] = t;
-  }
+    acc.add(v[i], v[i]);
+  block_partial<T>(acc, red, part);
 }
 
 // out = sum of partials (one CTA)
@@ -193,7 +257,7 @@ __global__ void k_zero(int n, T *x) {
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-int vec_grid() { return 2 * sm_count(); }
+int vec_grid() { return 4 * sm_count(); }
 
 // Workspace carving helper
 struct Carve {
@@ -221,9 +285,14 @@ struct CgMatrix {
 
 // Runs CG iterations on A p = ... with vectors of type T, starting from the
 // current x, r (p and rr set by k_cg_start).  Returns DAMN_OK or an error.
+// `chunk` iterations run per graph launch (even, so that parities line up);
+// the graph is captured on the first call and kept in *exec_cache (the
+// caller destroys it) for later calls with the same vectors, as the inner
+// solves of CG-IR are.
 template <typename T>
 int cg_loop(const CgMatrix &A, T *x, T *r, T *p, T *q, double *part_pq, double *part_rr,
-            CgScalars *sc, int max_iter, cudaStream_t s, int *iters_out, int *done_out) {
+            CgScalars *sc, int max_iter, cudaStream_t s, int *iters_out, int *done_out,
+            int chunk, cudaGraphExec_t *exec_cache) {
   const int n = A.n;
   const int gv = vec_grid();
   // the SpMV q = A p with the fused p.q partials
@@ -243,7 +312,6 @@ int cg_loop(const CgMatrix &A, T *x, T *r, T *p, T *q, double *part_pq, double *
   };
   CgScalars h{};
   int done_iters = 0;
-  const int chunk = 16;  // iterations per graph launch (even: parities line up)
   // first two iterations eagerly (launch attributes, SpMV grid size), then
   // graphs of `chunk` iterations; the device flag stops at convergence, at a
   // breakdown or at max_iter, after which launched iterations do nothing
@@ -251,8 +319,8 @@ int cg_loop(const CgMatrix &A, T *x, T *r, T *p, T *q, double *part_pq, double *
     int rc = iteration(k & 1);
     if (rc) return rc;
   }
-  cudaGraphExec_t exec = nullptr;
-  if (done_iters < max_iter) {
+  cudaGraphExec_t exec = *exec_cache;
+  if (!exec && done_iters < max_iter) {
     cudaStream_t cs;
     DAMN_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
@@ -272,6 +340,7 @@ int cg_loop(const CgMatrix &A, T *x, T *r, T *p, T *q, double *part_pq, double *
     cudaStreamDestroy(cs);
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_error(e, "cg graph capture");
+    *exec_cache = exec;
   }
   // chunks: launch, then read the flag (one small copy per chunk)
   int rc = DAMN_OK;
@@ -284,7 +353,6 @@ int cg_loop(const CgMatrix &A, T *x, T *r, T *p, T *q, double *part_pq, double *
     if (e != cudaSuccess) { rc = cuda_error(e, "cudaGraphLaunch"); break; }
     done_iters += chunk;
   }
-  if (exec) cudaGraphExecDestroy(exec);
   *iters_out = h.iters;
   *done_out = h.done;
   return rc;
@@ -372,7 +440,9 @@ extern "C" int damn_cg(int32_t n, int64_t nnz, const int32_t *rowptr, const int1
   k_cg_start<double><<<vec_grid(), kVecThreads, 0, s>>>(n, part_a, gs, sc, tol2, max_iter, r, p);
   DAMN_CHECK_LAUNCH("k_cg_start");
   int iters = 0, done = 0;
-  rc = cg_loop<double>(A, x, r, p, q, part_a, part_b, sc, max_iter, s, &iters, &done);
+  cudaGraphExec_t exec = nullptr;
+  rc = cg_loop<double>(A, x, r, p, q, part_a, part_b, sc, max_iter, s, &iters, &done, 16, &exec);
+  if (exec) cudaGraphExecDestroy(exec);
   if (rc) return rc;
   CgScalars h{};
   DAMN_CUDA(cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -440,6 +510,7 @@ extern "C" int damn_cg_ir(int32_t n, int64_t nnz, const int32_t *rowptr, const i
   int total_inner = 0, outer = 0;
   double relres = 0.0;
   bool converged = false;
+  cudaGraphExec_t inner_exec = nullptr;  // the inner loop's graph, captured once
   while (true) {
     // r = b - A x (FP64) and ||r||^2
     SpmvCall c;
@@ -448,41 +519,41 @@ extern "C" int damn_cg_ir(int32_t n, int64_t nnz, const int32_t *rowptr, const i
     c.alpha = -1.0; c.beta = 1.0; c.dot_self = 1; c.dot_partials = part_a;
     int gs = 0;
     rc = spmv_launch(c, plan64, s, &gs);
-    if (rc) return rc;
+    if (rc) break;
     k_sum<<<1, kVecThreads, 0, s>>>(part_a, gs, tmp);
-    DAMN_CHECK_LAUNCH("cg_ir residual");
     double rr = 0;
-    DAMN_CUDA(cudaMemcpyAsync(&rr, tmp, sizeof(double), cudaMemcpyDeviceToHost, s));
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&rr, tmp, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (ce != cudaSuccess) { rc = cuda_error(ce, "cg_ir residual"); break; }
     // also synchronises: a bounded wait that gave up inside an SpMV (this
     // residual or the previous inner solve) left vectors partly computed
     rc = check_device_status(s, "damn_cg_ir");
-    if (rc) return rc;
+    if (rc) break;
     relres = std::sqrt(rr) / nb;
     if (relres <= rtol) { converged = true; break; }
     if (outer >= max_outer || !std::isfinite(relres)) break;
-    // inner: A_low d = fl32(r / ||r||), d0 = 0, FP32 vectors, FP64 dots
+    // inner: A_low d = fl32(r / ||r||), d0 = 0, FP32 vectors, FP64 dots;
+    // tolerance relative to ||fl32(r / ||r||)||: k_cg_start forms
+    // tol2 = inner_rtol^2 * r32.r32 on the device from the same partials
     k_scale_to_f32<<<vec_grid(), kVecThreads, 0, s>>>(n, r, tmp, r32, d);
     k_dot_self<float><<<vec_grid(), kVecThreads, 0, s>>>(n, r32, part_a);
-    DAMN_CHECK_LAUNCH("cg_ir inner start");
-    // inner tolerance relative to ||fl32(r/||r||)||: tol2 = inner_rtol^2 * r32.r32,
-    // formed on the device by k_cg_start from the partials
-    k_sum<<<1, kVecThreads, 0, s>>>(part_a, vec_grid(), tmp + 2);
-    double ss = 0;
-    DAMN_CUDA(cudaMemcpyAsync(&ss, tmp + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
-    DAMN_CUDA(cudaStreamSynchronize(s));
     k_cg_start<float><<<vec_grid(), kVecThreads, 0, s>>>(n, part_a, vec_grid(), sc,
-                                                         inner_rtol * inner_rtol * ss, max_inner,
+                                                         -inner_rtol * inner_rtol, max_inner,
                                                          r32, p32);
-    DAMN_CHECK_LAUNCH("k_cg_start");
+    DAMN_CHECK_LAUNCH("cg_ir inner start");
     int it = 0, done = 0;
-    rc = cg_loop<float>(Alow, d, r32, p32, q32, part_a, part_b, sc, max_inner, s, &it, &done);
-    if (rc) return rc;
+    rc = cg_loop<float>(Alow, d, r32, p32, q32, part_a, part_b, sc, max_inner, s, &it, &done, 8,
+                        &inner_exec);
+    if (rc) break;
     total_inner += it;
     // x += ||r|| d
     k_ir_update<<<vec_grid(), kVecThreads, 0, s>>>(n, tmp, d, x);
-    DAMN_CHECK_LAUNCH("k_ir_update");
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) { rc = cuda_error(ce, "k_ir_update"); break; }
     ++outer;
   }
+  if (inner_exec) cudaGraphExecDestroy(inner_exec);
+  if (rc) return rc;
   h_res->iterations = total_inner;
   h_res->outer = outer;
   h_res->converged = converged ? 1 : 0;

@@ -223,6 +223,39 @@ __device__ __forceinline__ float to_acc(f8e4m3 v) {
   return __uint_as_float(__float_as_uint(f) | (static_cast<unsigned>(v.b & 0x80u) << 24));
 }
 
+// Running dot product of a thread.  FP64 operands: FP64 FMA.  FP32 operands
+// (the inner CG of the refinement): every product a b is split exactly into
+// FP32 p + e (e = fma(a, b, -p)), p is added to a compensated FP32 pair with
+// the error-free TwoSum, e and the TwoSum error go to the low part; the pair
+// is combined in FP64 once at the end.  The relative error of a thread's
+// sum of k products is below about (k + 2) 2^-47 (FP64 accumulation of the
+// same k products: k 2^-53), far below the FP32 rounding of the vectors,
+// and no FP64 instruction is spent per element (the FP64 unit of this part
+// does 2 lane operations per SM-cycle, the FP32 units 128).  Products below
+// FP32's normal range (|a b| < 2^-126) lose relative accuracy; the inner
+// vectors are normalised, far from that range.
+template <typename A> struct DotAcc;
+template <> struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = __fma_rn(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct DotAcc<float> {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);          // a b = p + pe exactly
+    const float s = __fadd_rn(hi, p);               // TwoSum(hi, p) = s + t exactly
+    const float bv = __fsub_rn(s, hi);
+    const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(t, pe));
+  }
+  __device__ __forceinline__ double value() const {
+    return static_cast<double>(hi) + static_cast<double>(lo);
+  }
+};
+
 __device__ __forceinline__ double fma_acc(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_acc(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 

@@ -324,7 +324,7 @@ struct DivK {
 template <bool PLAIN, class C, typename A>
 __device__ __forceinline__ void band_start_rows(const SpmvParams &p, const BandHdr &h,
                                                 const int *rp, int *srow, A *rowsum, int gtid,
-                                                double &dsum) {
+                                                DotAcc<A> &dsum) {
   const int nr = h.nr, k0 = h.k0;
   const int Kd = h.kd;
   DivK dk;
@@ -365,7 +365,8 @@ __device__ __forceinline__ void band_tile(const SpmvParams &p, const BandHdr &h,
                                           const typename AccOf<V>::type *ring, const int *srow,
                                           typename AccOf<V>::type *carry,
                                           typename AccOf<V>::type *rowsum, int gtid, int bar,
-                                          uint64_t *empty_s, double &dsum) {
+                                          uint64_t *empty_s,
+                                          DotAcc<typename AccOf<V>::type> &dsum) {
   using A = typename AccOf<V>::type;
   constexpr bool DA = sizeof(I) < 4;  // int16 / int8 offsets
   constexpr int CH = C::CH;
@@ -501,7 +502,7 @@ __global__ void __launch_bounds__(C::G * C::NT + 32, 1) k_spmv_band(const SpmvPa
   A *carry = reinterpret_cast<A *>(gsc + g * L::G_BYTES + L::G_CARRY);
   A *rowsum = reinterpret_cast<A *>(gsc + g * L::G_BYTES + L::G_ROWSUM);
   const int bar_a = 1 + 2 * g, bar_b = 2 + 2 * g;
-  double dsum = 0.0;
+  DotAcc<A> dsum;
   for (long long j = g; t0 + j < t1; j += C::G) {
     const int s = static_cast<int>(j % p.stages);
     const bool got = mbar_wait_bounded(&full[s], static_cast<uint32_t>((j / p.stages) & 1),
@@ -521,8 +522,9 @@ __global__ void __launch_bounds__(C::G * C::NT + 32, 1) k_spmv_band(const SpmvPa
                               dsum);
   }
   if (p.dot_partials) {
-    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-    if ((ctid & 31) == 0) red[ctid >> 5] = dsum;
+    double dv = dsum.value();
+    for (int o = 16; o > 0; o >>= 1) dv += __shfl_xor_sync(0xffffffffu, dv, o);
+    if ((ctid & 31) == 0) red[ctid >> 5] = dv;
     named_bar_sync(15, C::G * C::NT);
     if (ctid == 0) {
       double tot = 0.0;
@@ -548,7 +550,7 @@ template <bool PLAIN, typename V, typename I, class C>
 __device__ __forceinline__ void sorted_tile(const SpmvParams &p, const BandHdr &h, const int *rp,
                                             const uint16_t *perm, const V *vs, const I *is,
                                             const typename AccOf<V>::type *ring, int ctid,
-                                            double &dsum) {
+                                            DotAcc<typename AccOf<V>::type> &dsum) {
   using A = typename AccOf<V>::type;
   constexpr bool DA = sizeof(I) < 4;  // int16 / int8 offsets
   constexpr int CH = C::CH;
@@ -644,7 +646,7 @@ __global__ void __launch_bounds__(C::G * C::NT + 32, 1) k_spmv_sorted(const Spmv
     return;
   }
   const int ctid = tid - 32, g = ctid / C::NT, gtid = ctid % C::NT;
-  double dsum = 0.0;
+  DotAcc<A> dsum;
   // warps work independently: a warp whose bounded wait gives up stops
   for (long long j = g; t0 + j < t1; j += C::G) {
     const int s = static_cast<int>(j % p.stages);
@@ -669,8 +671,9 @@ __global__ void __launch_bounds__(C::G * C::NT + 32, 1) k_spmv_sorted(const Spmv
     if ((tid & 31) == 0) mbar_arrive(&empty[s]);
   }
   if (p.dot_partials) {
-    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-    if ((ctid & 31) == 0) red[ctid >> 5] = dsum;
+    double dv = dsum.value();
+    for (int o = 16; o > 0; o >>= 1) dv += __shfl_xor_sync(0xffffffffu, dv, o);
+    if ((ctid & 31) == 0) red[ctid >> 5] = dv;
     named_bar_sync(15, C::G * C::NT);
     if (ctid == 0) {
       double tot = 0.0;

@@ -450,7 +450,7 @@ struct XMap {
 // y[row] <- alpha acc + beta y0[row] (+ optional fused dot).  PLAIN is the
 // common y = A x case: no floating-point operation in the epilogue.
 template <bool PLAIN, typename A>
-__device__ __forceinline__ void store_row(const SpmvParams &p, int row, A acc, double &dsum) {
+__device__ __forceinline__ void store_row(const SpmvParams &p, int row, A acc, DotAcc<A> &dsum) {
   if (PLAIN) {
     static_cast<A *>(p.y)[row] = acc;
     return;
@@ -466,10 +466,9 @@ __device__ __forceinline__ void store_row(const SpmvParams &p, int row, A acc, d
   }
   static_cast<A *>(p.y)[row] = out;
   if (p.dot_w)
-    dsum = __fma_rn(static_cast<double>(static_cast<const A *>(p.dot_w)[row]),
-                    static_cast<double>(out), dsum);
+    dsum.add(static_cast<const A *>(p.dot_w)[row], out);
   else if (p.dot_self)
-    dsum = __fma_rn(static_cast<double>(out), static_cast<double>(out), dsum);
+    dsum.add(out, out);
 }
 
 // Pointers of a tile's values / indices / staged x (element 0 = entry k0).
@@ -514,7 +513,7 @@ __device__ __forceinline__ A x_at(const A *xg, const A *xs, const XM &xm, bool s
 // not in shared memory from global memory.
 template <bool PLAIN, typename V, typename I, class C>
 __device__ __noinline__ void rows_general(const SpmvParams &p, unsigned char *smem,
-                                          const TileHdr &h, int s, int ctid, double &dsum) {
+                                          const TileHdr &h, int s, int ctid, DotAcc<typename AccOf<V>::type> &dsum) {
   using A = typename AccOf<V>::type;
   constexpr bool DA = sizeof(I) < 4;  // int16 / int8 offsets
   TileView<V, I, C> tv;
@@ -543,7 +542,7 @@ __device__ __noinline__ void rows_general(const SpmvParams &p, unsigned char *sm
 template <bool PLAIN, typename V, typename I, class C, int NS>
 __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char *smem,
                                              uint64_t *full, uint64_t *empty, const TileHdr *hdr,
-                                             int ctid, double &dsum) {
+                                             int ctid, DotAcc<typename AccOf<V>::type> &dsum) {
   using L = Layout<V, I, C>;
   using A = typename AccOf<V>::type;
   constexpr bool DA = sizeof(I) < 4;  // int16 / int8 offsets
@@ -633,7 +632,7 @@ template <bool PLAIN, typename V, typename I, class C>
 __device__ __forceinline__ void tile_slices(const SpmvParams &p, const TileHdr &h,
                                             const TileView<V, I, C> &tv, int ctid,
                                             typename AccOf<V>::type *carry,
-                                            typename AccOf<V>::type *rowsum, double &dsum) {
+                                            typename AccOf<V>::type *rowsum, DotAcc<typename AccOf<V>::type> &dsum) {
   using A = typename AccOf<V>::type;
   constexpr bool DA = sizeof(I) < 4;  // int16 / int8 offsets
   constexpr int G = 8;
@@ -736,9 +735,9 @@ __global__ void __launch_bounds__(C::NT + 32, C::MINB) k_spmv(const SpmvParams p
     return;
   }
   const int ctid = tid - 32;
-  double dsum = 0.0;
+  DotAcc<A> dacc;
   if (p.mode == 0) {
-    consume_rows<PLAIN, V, I, C, NS>(p, smem, full, empty, hdr, ctid, dsum);
+    consume_rows<PLAIN, V, I, C, NS>(p, smem, full, empty, hdr, ctid, dacc);
   } else {
     int j = 0;
     for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++j) {
@@ -750,12 +749,13 @@ __global__ void __launch_bounds__(C::NT + 32, C::MINB) k_spmv(const SpmvParams p
       TileView<V, I, C> tv;
       tv.init(p, smem, h, s);
       tile_slices<PLAIN, V, I, C>(p, h, tv, ctid, carry + (j & 1) * C::NT,
-                                  rowsum + (j & 1) * C::CAP_ROWS, dsum);
+                                  rowsum + (j & 1) * C::CAP_ROWS, dacc);
       __syncwarp();
       if ((tid & 31) == 0) mbar_arrive(&empty[s]);
     }
   }
   if (p.dot_partials) {
+    double dsum = dacc.value();
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
     if ((ctid & 31) == 0) red[ctid >> 5] = dsum;
     named_bar_sync(3, C::NT);

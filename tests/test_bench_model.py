@@ -52,7 +52,7 @@ def test_recorded_traffic_only_for_the_profiled_source(monkeypatch):
 
 def test_kernel_source_hash_ignores_comments(tmp_path, monkeypatch):
     src = os.path.join(bench.ROOT, "paper_2307_06305_gb300", "csrc")
-    names = ("spmv_kernel.cuh", "spmv.cu", "damn_common.cuh")
+    names = ("spmv_kernel.cuh", "spmv_launch.cuh", "spmv.cu", "damn_common.cuh")
     for name in names:
         with open(os.path.join(src, name)) as f:
             (tmp_path / name).write_text(f.read())
