@@ -144,6 +144,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   }
 }
 
+// Programmatic dependent launch.  wait: blocks until the grids this one
+// depends on in its stream have completed and their writes are visible (a
+// no-op when the launch did not ask for programmatic serialisation); no
+// global memory may be touched before it.  launch_dependents: lets the next
+// kernel of the stream start launching its CTAs (they run their prologue,
+// then wait in turn), hiding the launch gap between back-to-back kernels.
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }

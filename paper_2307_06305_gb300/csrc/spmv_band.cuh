@@ -491,6 +491,8 @@ __global__ void __launch_bounds__(C::G * C::NT + 32, 1) k_spmv_band(const SpmvPa
     fence_mbar_init();
   }
   __syncthreads();
+  grid_dependency_wait();  // global memory only after the previous kernel
+  grid_launch_dependents();
   long long t0, t1;
   band_chunk(p.ntiles, blockIdx.x, gridDim.x, t0, t1);
   if (tid < 32) {
@@ -639,6 +641,8 @@ __global__ void __launch_bounds__(C::G * C::NT + 32, 1) k_spmv_sorted(const Spmv
     fence_mbar_init();
   }
   __syncthreads();
+  grid_dependency_wait();  // global memory only after the previous kernel
+  grid_launch_dependents();
   long long t0, t1;
   band_chunk(p.ntiles, blockIdx.x, gridDim.x, t0, t1);
   if (tid < 32) {

@@ -730,6 +730,10 @@ __global__ void __launch_bounds__(C::NT + 32, C::MINB) k_spmv(const SpmvParams p
     fence_mbar_init();
   }
   __syncthreads();
+  // shared-memory set-up above overlaps the previous kernel of the stream;
+  // global memory only after it has completed
+  grid_dependency_wait();
+  grid_launch_dependents();
   if (tid < 32) {
     produce<V, I, C>(p, smem, full, empty, hdr);
     return;

@@ -70,6 +70,28 @@ int pick_geometry(KFn kernel, int threads, TotalFn total, int minb, int req, Occ
   return DAMN_OK;
 }
 
+// Launches kernel<<<grid, threads, smem, s>>>(p) with programmatic stream
+// serialisation: the kernel may begin launching while the previous kernel
+// of the stream finishes; it waits for it (griddepcontrol.wait) before
+// touching global memory.
+template <class KFn>
+int launch_pdl(KFn kernel, int grid, int threads, size_t smem, cudaStream_t s,
+               const SpmvParams &p, const char *what) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, p);
+  if (e != cudaSuccess) return cuda_error(e, what);
+  return DAMN_OK;
+}
+
 template <bool PLAIN, typename V, typename I, class C, int NS>
 int launch_kernel(SpmvParams p, cudaStream_t s, int *gs_out) {
   using L = Layout<V, I, C>;
@@ -85,9 +107,8 @@ int launch_kernel(SpmvParams p, cudaStream_t s, int *gs_out) {
   const int grid = std::max(1, std::min(p.ntiles, occ * sm_count()));
   if (gs_out) { gs_out[0] = grid; gs_out[1] = p.stages; }
   if (p.ntiles == 0) return DAMN_OK;
-  k_spmv<PLAIN, V, I, C, NS><<<grid, C::NT + 32, L::total(p.stages, mode), s>>>(p);
-  DAMN_CHECK_LAUNCH("k_spmv");
-  return DAMN_OK;
+  return launch_pdl(k_spmv<PLAIN, V, I, C, NS>, grid, C::NT + 32, L::total(p.stages, mode), s, p,
+                    "k_spmv");
 }
 
 template <bool PLAIN, typename V, typename I, class C>
@@ -105,9 +126,8 @@ int launch_band(SpmvParams p, cudaStream_t s, int *gs_out) {
   const int grid = std::max(1, std::min(occ * sm_count(), (p.ntiles + 3) / 4));
   if (gs_out) { gs_out[0] = grid; gs_out[1] = p.stages; }
   if (p.ntiles == 0) return DAMN_OK;
-  k_spmv_band<PLAIN, V, I, C><<<grid, C::G * C::NT + 32, L::total(p.stages), s>>>(p);
-  DAMN_CHECK_LAUNCH("k_spmv_band");
-  return DAMN_OK;
+  return launch_pdl(k_spmv_band<PLAIN, V, I, C>, grid, C::G * C::NT + 32, L::total(p.stages), s,
+                    p, "k_spmv_band");
 }
 
 template <bool PLAIN, typename V, typename I, class C>
@@ -124,9 +144,8 @@ int launch_sorted(SpmvParams p, cudaStream_t s, int *gs_out) {
   const int grid = std::max(1, std::min(occ * sm_count(), (p.ntiles + 3) / 4));
   if (gs_out) { gs_out[0] = grid; gs_out[1] = p.stages; }
   if (p.ntiles == 0) return DAMN_OK;
-  k_spmv_sorted<PLAIN, V, I, C><<<grid, C::G * C::NT + 32, L::total(p.stages), s>>>(p);
-  DAMN_CHECK_LAUNCH("k_spmv_sorted");
-  return DAMN_OK;
+  return launch_pdl(k_spmv_sorted<PLAIN, V, I, C>, grid, C::G * C::NT + 32, L::total(p.stages),
+                    s, p, "k_spmv_sorted");
 }
 
 inline bool is_plain(const SpmvParams &p) {
