@@ -233,6 +233,8 @@ typedef struct {
                            whose ring is filled as the kernel runs)           */
   int32_t stages_requested; /* ring depth set by damn_plan_set_stages or the
                            autotuner (0: automatic)                           */
+  int32_t x_staging;     /* rows tilings: 1 = x windows staged in shared
+                           memory, 0 = x read from global memory (L1 / L2)    */
 } damn_plan_desc;
 
 /* Tilings (see damn_plan_set_tiling). */
@@ -275,7 +277,9 @@ int damn_plan_create(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *r
  * 4 / 8 / 16 / 32 lanes per row where an average row has
  * at least two entries per lane -- keeps the fastest, then times ring depths
  * of 2 to 6 stages for it and keeps one only when it is at least 3 % faster
- * than the automatic depth.  y is overwritten.  Synchronises stream. */
+ * than the automatic depth, then (rows tilings) times x read from global
+ * memory instead of staged, kept on the same 3 % rule.  y is overwritten.
+ * Synchronises stream. */
 int damn_plan_autotune(damn_plan *plan, int format, const void *idx, const void *val,
                        const void *x, void *y, void *stream);
 
@@ -311,6 +315,14 @@ int damn_plan_set_tiling(damn_plan *plan, int tiling);
  * that take turns on the tiles; their depth is rounded down to a multiple of
  * the number of groups (4 and 2).  No device work. */
 int damn_plan_set_stages(damn_plan *plan, int32_t stages);
+
+/* Rows tilings (DAMN_TILING_ROWS*, ROWS_LONG, ROWS_LANES*): on != 0 (the
+ * default) stages each tile's x window in shared memory; on == 0 reads x
+ * from global memory (L1 / L2) instead, with the same register-batched row
+ * loop -- cheaper per entry when a warp's rows read consecutive x entries at
+ * each offset (stencil-like patterns).  Results are bitwise the same either
+ * way.  No device work.  The autotuner tries both for rows tilings. */
+int damn_plan_set_x_staging(damn_plan *plan, int32_t on);
 
 int damn_plan_describe(const damn_plan *plan, damn_plan_desc *h_desc);
 int damn_plan_destroy(damn_plan *plan);

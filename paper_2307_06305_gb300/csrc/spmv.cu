@@ -402,6 +402,7 @@ struct damn_plan {
   double row_eff;
   int max_tile_short, max_tile_long;
   int stages_req;         // requested ring depth (0: automatic)
+  int no_xstage;          // rows tilings: read x from global memory, stage no x window
   int grid, stages;       // geometry of the last launch
 };
 
@@ -496,7 +497,7 @@ static int make_params(const SpmvCall &c, const damn_plan *plan, SpmvParams &p, 
     p.rows_per_tile = plan->rows_per_tile;
     p.ntiles = plan->ntiles;
     p.bounds = plan->d_bounds;
-    p.xseg = plan->mode >= 2 ? nullptr : plan->d_xseg;
+    p.xseg = (plan->mode >= 2 || (plan->mode == 0 && plan->no_xstage)) ? nullptr : plan->d_xseg;
     p.colrange = plan->mode == 2 ? plan->d_colrange
                  : plan->mode == 3 ? plan->d_colrange_sorted : nullptr;
     p.perm = plan->mode == 3 ? plan->d_perm : nullptr;
@@ -883,6 +884,7 @@ extern "C" int damn_plan_autotune(damn_plan *plan, int format, const void *idx, 
     if (mean >= 2.0 * (4 << i)) cands[nc++] = lane_t[i];
   const int keep_stages = plan->stages_req;
   plan->stages_req = 0;
+  plan->no_xstage = 0;
   float best_ms = 1e30f;
   int best = plan_tiling_of(plan);
   for (int ci = 0; ci < nc && rc == DAMN_OK; ++ci) {
@@ -902,6 +904,14 @@ extern "C" int damn_plan_autotune(damn_plan *plan, int format, const void *idx, 
     if (t < 0.97f * best_ms) { best_ms = t; best_st = st; }
   }
   plan->stages_req = rc ? keep_stages : best_st;
+  // 3. rows tilings: x staged in shared memory, or read from L1 / L2
+  if (!rc && plan->mode == 0 && plan->d_xseg) {
+    plan->no_xstage = 1;
+    float t = 1e30f;
+    rc = time_plan(&t);
+    if (rc || !(t < 0.97f * best_ms)) plan->no_xstage = 0;
+    else best_ms = t;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return rc;
@@ -912,6 +922,12 @@ extern "C" int damn_plan_set_tiling(damn_plan *plan, int tiling) {
   if (shape_of_tiling(tiling) < 0)
     return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_set_tiling: bad tiling %d", tiling);
   return plan_use(plan, tiling, nullptr);
+}
+
+extern "C" int damn_plan_set_x_staging(damn_plan *plan, int32_t on) {
+  if (!plan) return set_error(DAMN_ERR_INVALID_ARG, "damn_plan_set_x_staging: plan is NULL");
+  plan->no_xstage = on ? 0 : 1;
+  return DAMN_OK;
 }
 
 extern "C" int damn_plan_set_stages(damn_plan *plan, int32_t stages) {
@@ -939,6 +955,7 @@ extern "C" int damn_plan_describe(const damn_plan *plan, damn_plan_desc *h_desc)
   h_desc->tiling = plan_tiling_of(plan);
   h_desc->x_staged_tiles = plan->staged_tiles;
   h_desc->stages_requested = plan->stages_req;
+  h_desc->x_staging = plan->no_xstage ? 0 : 1;
   return DAMN_OK;
 }
 

@@ -539,6 +539,10 @@ __device__ __noinline__ void rows_general(const SpmvParams &p, unsigned char *sm
 // loads its rows' values and x into registers, hands the stage back, then
 // runs the FMA chains, so the warps of a CTA do not wait for each other.
 // Rows longer than U entries finish from the stage before it is released.
+// NS = 0: the plan stages no x window; x is read from global memory (L1 /
+// L2) in the same register-batched way -- for stencil-like rows the lanes of
+// a warp read consecutive x entries at each offset, and no column -> slot
+// map is computed per entry.
 template <bool PLAIN, typename V, typename I, class C, int NS>
 __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char *smem,
                                              uint64_t *full, uint64_t *empty, const TileHdr *hdr,
@@ -554,7 +558,7 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
     if (!mbar_wait_bounded(&full[s], (j / p.stages) & 1, p.status, p.timeout_ns)) return;
     const int4 *hv = reinterpret_cast<const int4 *>(&hdr[s]);
     const int4 h0 = hv[0];  // r0, nr, k0, flags
-    if (h0.w != kTileStaged) {
+    if (NS > 0 ? h0.w != kTileStaged : (h0.w & kTileDirect) != 0) {
       rows_general<PLAIN, V, I, C>(p, smem, hdr[s], s, ctid, dsum);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
@@ -562,13 +566,18 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
     }
     const int4 h1 = hv[1];  // rp_sh, v_sh, i_sh, d0
     XMap<L::X_ELEMS> xm;
-    xm.load(hdr[s]);
+    if (NS > 0) xm.load(hdr[s]);
     unsigned char *st = smem + (size_t)s * L::STAGE;
     const int *rp = reinterpret_cast<const int *>(st) + h1.x;
     const V *vs = reinterpret_cast<const V *>(st + L::OFF_V) + h1.y;
     const I *is = reinterpret_cast<const I *>(st + L::OFF_I) + h1.z;
     const A *xs = reinterpret_cast<const A *>(st + L::OFF_X);
+    const A *xg = static_cast<const A *>(p.x);
     const int r0 = h0.x, nr = h0.y, k0 = h0.z;
+    auto xval = [&](int cl) -> A {
+      if constexpr (NS == 0) return x_global(xg, r0 + cl, p.ncols);
+      else return xs[xm.template slot_n<NS>(cl)];
+    };
     // lane ei of the E lanes of a row takes the row's entries ei, ei + E, ...
     constexpr int E = C::E;
     constexpr int UL = U / E;  // entries per lane kept in registers
@@ -593,7 +602,7 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
           const int cl = DA ? lr + static_cast<int>(is[b[rr] + q])
                             : static_cast<int>(is[b[rr] + q]) - r0;
           av[rr][u] = to_acc(vs[b[rr] + q]);
-          xv[rr][u] = xs[xm.template slot_n<NS>(cl)];
+          xv[rr][u] = xval(cl);
         }
       }
       fits = fits && cnt[rr] <= U;
@@ -614,7 +623,7 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
       for (int q = ei + UL * E; q < cnt[rr]; q += E) {  // rows longer than U
         const int cl = DA ? lr + static_cast<int>(is[b[rr] + q])
                           : static_cast<int>(is[b[rr] + q]) - r0;
-        acc = fma_acc(to_acc(vs[b[rr] + q]), xs[xm.template slot_n<NS>(cl)], acc);
+        acc = fma_acc(to_acc(vs[b[rr] + q]), xval(cl), acc);
       }
 #pragma unroll
       for (int o = 1; o < E; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

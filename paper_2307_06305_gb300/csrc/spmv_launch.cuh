@@ -157,6 +157,13 @@ int launch_cfg(const SpmvParams &p, cudaStream_t s, int *gs) {
   const bool plain = is_plain(p);
   // one row per lane with every x window of at most 3 segments: one compare
   // fewer per entry in the column -> slot map
+  if constexpr (C::E <= 2) {
+    // rows without x windows: x read from global memory in the batched path
+    if (p.mode == 0 && !p.xseg) {
+      if (plain) return launch_kernel<true, V, I, C, 0>(p, s, gs);
+      return launch_kernel<false, V, I, C, 0>(p, s, gs);
+    }
+  }
   if constexpr (C::E == 1) {
     if (p.mode == 0 && p.max_nseg <= 3) {
       if (plain) return launch_kernel<true, V, I, C, 3>(p, s, gs);

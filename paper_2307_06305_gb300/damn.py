@@ -72,7 +72,7 @@ class damn_plan_desc(ctypes.Structure):
     _fields_ = [("mode", I32), ("tile_items", I32), ("ntiles", I32), ("grid", I32),
                 ("stages", I32), ("threads", I32), ("row_efficiency", F64), ("max_row", I32),
                 ("dtype", I32), ("tiling", I32), ("x_staged_tiles", I32),
-                ("stages_requested", I32)]
+                ("stages_requested", I32), ("x_staging", I32)]
 
 
 class damn_cg_result(ctypes.Structure):
@@ -119,6 +119,7 @@ _sig("damn_plan_autotune", ctypes.c_int, [P, ctypes.c_int, P, P, P, P, P])
 _sig("damn_plan_describe", ctypes.c_int, [P, ctypes.POINTER(damn_plan_desc)])
 _sig("damn_plan_set_tiling", ctypes.c_int, [P, ctypes.c_int])
 _sig("damn_plan_set_stages", ctypes.c_int, [P, I32])
+_sig("damn_plan_set_x_staging", ctypes.c_int, [P, I32])
 _sig("damn_plan_destroy", ctypes.c_int, [P])
 _sig("damn_spmv_csr32", ctypes.c_int,
      [I32, I32, I64, P, P, P, ctypes.c_int, P, P, F64, F64, P, P])
@@ -333,6 +334,12 @@ class Plan:
 
     def set_tiling(self, tiling: int):
         _check(_lib.damn_plan_set_tiling(self.handle, int(tiling)), "damn_plan_set_tiling")
+        return self
+
+    def set_x_staging(self, on: bool):
+        """Rows tilings: stage x windows in shared memory (True) or read x
+        from global memory (False)."""
+        _check(_lib.damn_plan_set_x_staging(self.handle, int(bool(on))), "damn_plan_set_x_staging")
         return self
 
     def set_stages(self, stages: int):
