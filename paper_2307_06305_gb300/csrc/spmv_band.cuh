@@ -180,15 +180,15 @@ template <typename V, typename I, class C>
 __device__ __forceinline__ bool band_issue(const SpmvParams &p, unsigned char *smem,
                                            typename AccOf<V>::type *ring, uint64_t *full,
                                            uint64_t *empty, BandHdr *hdr, const BandIssue &bi,
-                                           long long j, uint64_t pol, int &F, int &vrun) {
+                                           long long j, RingPos rp, uint64_t pol, int &F,
+                                           int &vrun) {
   using L = BandLayout<V, I, C>;
   using A = typename L::A;
   constexpr int EX = L::EX;
   const int S = p.stages;
-  const int s = static_cast<int>(j % S);
-  if (j >= S && !mbar_wait_bounded(&empty[s], static_cast<uint32_t>(((j / S) - 1) & 1), p.status,
-                                   p.timeout_ns))
-    return false;
+  const int s = rp.s;
+  // the stage's previous pass (tile j - S) must have been consumed
+  if (j >= S && !mbar_wait_bounded(&empty[s], rp.ph ^ 1u, p.status, p.timeout_ns)) return false;
   unsigned char *st = smem + (size_t)s * L::STAGE;
   int *rp_s = reinterpret_cast<int *>(st);
   V *v_s = reinterpret_cast<V *>(st + L::OFF_V);
@@ -259,6 +259,7 @@ __device__ __forceinline__ void band_produce(const SpmvParams &p, unsigned char 
   const uint64_t pol = l2_policy_evict_first();
   int F = -1, vrun = 0;
   long long j = 0;
+  RingPos rpos;  // ring position of tile j (the same in every lane)
   bool stop = false;
   while (!stop && t0 + j < t1) {
     BandIssue bi;
@@ -266,12 +267,14 @@ __device__ __forceinline__ void band_produce(const SpmvParams &p, unsigned char 
     for (int i = 0; i < 32; ++i) {
       if (t0 + j >= t1) { stop = true; break; }
       int ok = 1;
-      if (lane == i) ok = band_issue<V, I, C>(p, smem, ring, full, empty, hdr, bi, j, pol, F, vrun);
+      if (lane == i)
+        ok = band_issue<V, I, C>(p, smem, ring, full, empty, hdr, bi, j, rpos, pol, F, vrun);
       ok = __shfl_sync(0xffffffffu, ok, i);
       F = __shfl_sync(0xffffffffu, F, i);
       vrun = __shfl_sync(0xffffffffu, vrun, i);
       if (!ok) { stop = true; break; }
       ++j;
+      rpos.advance(1, p.stages);
     }
   }
   // no copies left in flight: wait (bounded) for the last issued stages
@@ -410,12 +413,25 @@ __device__ __forceinline__ void band_tile(const SpmvParams &p, const BandHdr &h,
         }
       }
       A av[CH], xv[CH];
+      // one loop per x source (the choice is the tile's): a per-entry select
+      // would issue both loads under predicates
+      if (from_ring) {
 #pragma unroll
-      for (int u = 0; u < CH; ++u) {
-        if (q + u < qe) {
-          const int c = DA ? r0 + lrow[u] + static_cast<int>(is[q + u]) : static_cast<int>(is[q + u]);
-          av[u] = to_acc(vs[q + u]);
-          xv[u] = from_ring ? ring[c & (C::W - 1)] : x_global(xg, c, p.ncols);
+        for (int u = 0; u < CH; ++u) {
+          if (q + u < qe) {
+            const int c = DA ? r0 + lrow[u] + static_cast<int>(is[q + u]) : static_cast<int>(is[q + u]);
+            av[u] = to_acc(vs[q + u]);
+            xv[u] = ring[c & (C::W - 1)];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          if (q + u < qe) {
+            const int c = DA ? r0 + lrow[u] + static_cast<int>(is[q + u]) : static_cast<int>(is[q + u]);
+            av[u] = to_acc(vs[q + u]);
+            xv[u] = x_global(xg, c, p.ncols);
+          }
         }
       }
 #pragma unroll
@@ -505,10 +521,11 @@ __global__ void __launch_bounds__(C::G * C::NT + 32, 1) k_spmv_band(const SpmvPa
   A *rowsum = reinterpret_cast<A *>(gsc + g * L::G_BYTES + L::G_ROWSUM);
   const int bar_a = 1 + 2 * g, bar_b = 2 + 2 * g;
   DotAcc<A> dsum;
-  for (long long j = g; t0 + j < t1; j += C::G) {
-    const int s = static_cast<int>(j % p.stages);
-    const bool got = mbar_wait_bounded(&full[s], static_cast<uint32_t>((j / p.stages) & 1),
-                                       p.status, p.timeout_ns);
+  RingPos rpos;
+  rpos.s = g;  // tile g: the depth is a multiple of G, so g < stages and parity 0
+  for (long long j = g; t0 + j < t1; j += C::G, rpos.advance(C::G, p.stages)) {
+    const int s = rpos.s;
+    const bool got = mbar_wait_bounded(&full[s], rpos.ph, p.status, p.timeout_ns);
     const BandHdr &h = hdr[s];
     unsigned char *st = smem + (size_t)s * L::STAGE;
     const int *rp = reinterpret_cast<const int *>(st) + h.rp_sh;
@@ -652,11 +669,11 @@ __global__ void __launch_bounds__(C::G * C::NT + 32, 1) k_spmv_sorted(const Spmv
   const int ctid = tid - 32, g = ctid / C::NT, gtid = ctid % C::NT;
   DotAcc<A> dsum;
   // warps work independently: a warp whose bounded wait gives up stops
-  for (long long j = g; t0 + j < t1; j += C::G) {
-    const int s = static_cast<int>(j % p.stages);
-    if (!mbar_wait_bounded(&full[s], static_cast<uint32_t>((j / p.stages) & 1), p.status,
-                           p.timeout_ns))
-      break;
+  RingPos rpos;
+  rpos.s = g;  // tile g: the depth is a multiple of G, so g < stages and parity 0
+  for (long long j = g; t0 + j < t1; j += C::G, rpos.advance(C::G, p.stages)) {
+    const int s = rpos.s;
+    if (!mbar_wait_bounded(&full[s], rpos.ph, p.status, p.timeout_ns)) break;
     const BandHdr &h = hdr[s];
     unsigned char *st = smem + (size_t)s * L::STAGE;
     const int *rp = reinterpret_cast<const int *>(st) + h.rp_sh;

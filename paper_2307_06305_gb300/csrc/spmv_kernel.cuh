@@ -212,6 +212,19 @@ struct Layout {
   }
 };
 
+// Position in the ring of shared-memory stages: the stage of a tile and the
+// phase parity of that stage's pass, advanced by additions instead of the
+// division tile / stages (a run-time 32- or 64-bit division costs dozens to
+// hundreds of instructions per tile).
+struct RingPos {
+  int s = 0;        // stage
+  uint32_t ph = 0;  // parity of the current pass over the ring
+  __device__ __forceinline__ void advance(int by, int stages) {  // by <= stages
+    s += by;
+    if (s >= stages) { s -= stages; ph ^= 1u; }
+  }
+};
+
 // Element range [first, first+count) of an array of len elements, split into a
 // 16-byte aligned bulk part [a0, b1) and a plainly loaded tail [tb, first+count)
 // beyond the array's last full 16-byte block.
@@ -337,12 +350,13 @@ __device__ __forceinline__ void prepare_tile(const SpmvParams &p, long long t, T
 template <typename V, typename I, class C>
 __device__ __forceinline__ bool issue_tile(const SpmvParams &p, unsigned char *smem, uint64_t *full,
                                            uint64_t *empty, TileHdr *hdr, const TileIssue &ti,
-                                           int j, uint64_t pol) {
+                                           int j, RingPos rp, uint64_t pol) {
   using L = Layout<V, I, C>;
   using A = typename L::A;
   const int S = p.stages;
-  const int s = j % S;
-  if (j >= S && !mbar_wait_bounded(&empty[s], ((j / S) - 1) & 1, p.status, p.timeout_ns))
+  const int s = rp.s;
+  // the stage's previous pass (tile j - S) must have been consumed
+  if (j >= S && !mbar_wait_bounded(&empty[s], rp.ph ^ 1u, p.status, p.timeout_ns))
     return false;
   unsigned char *st = smem + (size_t)s * L::STAGE;
   int *rp_s = reinterpret_cast<int *>(st);
@@ -390,20 +404,21 @@ __device__ __forceinline__ void produce(const SpmvParams &p, unsigned char *smem
   const int lane = threadIdx.x & 31;
   const uint64_t pol = l2_policy_evict_first();
   int j = 0;
+  RingPos rpos;  // ring position of tile j (the same in every lane)
   bool stop = false;
   while (!stop) {
     const long long tl = (long long)blockIdx.x + (long long)(j + lane) * gridDim.x;
     TileIssue ti;
     if (tl < p.ntiles) prepare_tile<V, I, C>(p, tl, ti);
-    const int jl = j + lane;
     for (int i = 0; i < 32; ++i) {
       const long long t = (long long)blockIdx.x + (long long)j * gridDim.x;
       if (t >= p.ntiles) { stop = true; break; }
       int ok = 1;
-      if (lane == i) ok = issue_tile<V, I, C>(p, smem, full, empty, hdr, ti, jl, pol) ? 1 : 0;
+      if (lane == i) ok = issue_tile<V, I, C>(p, smem, full, empty, hdr, ti, j, rpos, pol) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, i);
       if (!ok) { stop = true; break; }
       ++j;
+      rpos.advance(1, p.stages);
     }
   }
   // Do not leave copies in flight: wait (bounded) for the last issued stages.
@@ -552,10 +567,10 @@ __device__ __forceinline__ void consume_rows(const SpmvParams &p, unsigned char 
   constexpr bool DA = sizeof(I) < 4;  // int16 / int8 offsets
   constexpr int U = C::CAP_NZ / C::TILE_ROWS;
   const int lane = threadIdx.x & 31;
-  int j = 0;
-  for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++j) {
-    const int s = j % p.stages;
-    if (!mbar_wait_bounded(&full[s], (j / p.stages) & 1, p.status, p.timeout_ns)) return;
+  RingPos rpos;
+  for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, rpos.advance(1, p.stages)) {
+    const int s = rpos.s;
+    if (!mbar_wait_bounded(&full[s], rpos.ph, p.status, p.timeout_ns)) return;
     const int4 *hv = reinterpret_cast<const int4 *>(&hdr[s]);
     const int4 h0 = hv[0];  // r0, nr, k0, flags
     if (NS > 0 ? h0.w != kTileStaged : (h0.w & kTileDirect) != 0) {
@@ -752,10 +767,12 @@ __global__ void __launch_bounds__(C::NT + 32, C::MINB) k_spmv(const SpmvParams p
   if (p.mode == 0) {
     consume_rows<PLAIN, V, I, C, NS>(p, smem, full, empty, hdr, ctid, dacc);
   } else {
-    int j = 0;
-    for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++j) {
-      const int s = j % p.stages;
-      const bool got = mbar_wait_bounded(&full[s], (j / p.stages) & 1, p.status, p.timeout_ns);
+    RingPos rpos;
+    int j = 0;  // tile count: the slice scratch is double-buffered by its parity
+    for (long long t = blockIdx.x; t < p.ntiles;
+         t += gridDim.x, rpos.advance(1, p.stages), ++j) {
+      const int s = rpos.s;
+      const bool got = mbar_wait_bounded(&full[s], rpos.ph, p.status, p.timeout_ns);
       // the consumers synchronise inside a tile, so they give up together
       if (named_bar_or(2, C::NT, !got)) break;
       const TileHdr &h = hdr[s];
