@@ -336,21 +336,10 @@ __device__ __forceinline__ void band_start_rows(const SpmvParams &p, const BandH
     const int b = rp[lr] - k0, e = rp[lr + 1] - k0;
     if (e > b) {
       for (int t = dk.div(b + Kd - 1); t * Kd < e; ++t) srow[t] = lr;
-    } else if (PLAIN) {
-      store_row<true>(p, h.r0 + lr, A(0), dsum);
     } else {
       rowsum[lr] = A(0);
     }
   }
-}
-
-// A row's sum is complete: PLAIN stores it at once, otherwise it is kept for
-// the tile's epilogue pass (alpha, beta and the fused dot with all lanes).
-template <bool PLAIN, typename A>
-__device__ __forceinline__ void band_row_done(const SpmvParams &p, int r0, int lr, A acc,
-                                              A *rowsum) {
-  if (PLAIN) static_cast<A *>(p.y)[r0 + lr] = acc;
-  else rowsum[lr] = acc;
 }
 
 // Steps 2 and 3 of a tile: the thread's slice, then (after the group
@@ -434,22 +423,23 @@ __device__ __forceinline__ void band_tile(const SpmvParams &p, const BandHdr &h,
           }
         }
       }
+      // The FMA first, for every lane at once (the accumulator reset by a
+      // mask, not a branch); a row that ended just before this entry goes to
+      // the tile's row sums by a predicated shared-memory store (the first
+      // row of the slice, when it began in an earlier slice, is finished
+      // after the barrier; its partial sum is kept in a register).
 #pragma unroll
       for (int u = 0; u < CH; ++u) {
         if (q + u < qe) {
-          // the FMA first, for every lane at once (the accumulator reset by
-          // a mask, not a branch); then the rare bookkeeping of a row that
-          // ended just before this entry
           const int prev = row;
           const bool nb = lrow[u] != prev;
           const A done = acc;
           acc = fma_acc(av[u], xv[u], zero_if(nb, acc));
           row = lrow[u];
-          if (nb) {
-            if (first && open) { pend_row = prev; pend_acc = done; pend_b = rb; }
-            else band_row_done<PLAIN>(p, r0, prev, done, rowsum);
-            first = false;
-          }
+          const bool pend_now = nb && first && open;
+          pend_acc = pend_now ? done : pend_acc;
+          if (nb && !pend_now) rowsum[prev] = done;
+          first = first && !nb;
         }
       }
       if (qe < e0) {  // another chunk: row ends from the current row on
@@ -459,11 +449,12 @@ __device__ __forceinline__ void band_tile(const SpmvParams &p, const BandHdr &h,
     }
     const int rend = rp[row + 1] - k0;
     if (rend == e0) {  // the slice's last row ends with the slice
-      if (first && open) { pend_row = row; pend_acc = acc; pend_b = rb; }
-      else band_row_done<PLAIN>(p, r0, row, acc, rowsum);
+      if (first && open) pend_acc = acc;
+      else rowsum[row] = acc;
     } else {
       carry[gtid] = acc;  // continues into the next slice
     }
+    if (open && (rend == e0 || !first)) { pend_row = srow[gtid]; pend_b = rb; }
   }
   // every read of the stage and of the ring for this tile is done
   __syncwarp();
@@ -475,12 +466,12 @@ __device__ __forceinline__ void band_tile(const SpmvParams &p, const BandHdr &h,
     const int a = dk.div(pend_b);  // the slice where the row began
     A tot = carry[a];
     for (int t = a + 1; t < gtid; ++t) tot += carry[t];
-    band_row_done<PLAIN>(p, r0, pend_row, tot + pend_acc, rowsum);
+    rowsum[pend_row] = tot + pend_acc;
   }
-  if (!PLAIN) {
-    named_bar_sync(bar, C::NT);
-    for (int lr = gtid; lr < nr; lr += C::NT) store_row<false>(p, r0 + lr, rowsum[lr], dsum);
-  }
+  // y for the tile's rows in one coalesced pass (alpha, beta and the fused
+  // dot, if any, with all lanes)
+  named_bar_sync(bar, C::NT);
+  for (int lr = gtid; lr < nr; lr += C::NT) store_row<PLAIN>(p, r0 + lr, rowsum[lr], dsum);
 }
 
 // ----------------------------------------------------------------------------
