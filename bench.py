@@ -809,7 +809,7 @@ def main():
     ap.add_argument("--e2e-parts", type=int, default=1,
                     help="parts (streams) each end-to-end upload / download is split into")
     ap.add_argument("--tiling", default="auto", choices=["auto"] + list(TILING_NAMES),
-                    help="headline plan tiling: autotuned, or fixed")
+                    help="plan tiling of the headline and mixed-precision plans: autotuned, or fixed")
     ap.add_argument("--case", default=None, type=profile_case,
                     help="run only the launches of one profiled kernel (for ncu), no timing")
     args = ap.parse_args()
@@ -929,7 +929,10 @@ def main():
         x32 = t_x.float()
         y32 = torch.empty(n, dtype=torch.float32, device=dev)
         pl = [D.Plan(t_rp[c], nnz, n, dt, idx=t_off[c]) for c in range(NCOPY)]
-        pl[0].autotune(D.DAMN_FMT_DACSR16, t_off[0], vals[0], x32, y32)
+        if args.tiling == "auto":
+            pl[0].autotune(D.DAMN_FMT_DACSR16, t_off[0], vals[0], x32, y32)
+        else:  # a pinned tiling also pins these plans (a profiled run stays deterministic)
+            pl[0].set_tiling(TILING_NAMES.index(args.tiling))
         dsc = pl[0].describe()
         for c in range(1, NCOPY):
             pl[c].set_tiling(dsc["tiling"])

@@ -8,6 +8,8 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 #include <mutex>
 #include <string>
@@ -225,15 +227,11 @@ template <> struct AccOf<f8e4m3> { using type = float; };
 __device__ __forceinline__ double to_acc(double v) { return v; }
 __device__ __forceinline__ float to_acc(float v) { return v; }
 __device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
-// E4M3 -> FP32, exact: the 7 magnitude bits placed at the top of an FP32
-// exponent field give 2^(e-127) (1 + m/8) for e > 0 and, as an FP32
-// subnormal, m 2^-129 for e = 0; one multiplication by 2^120 moves both to
-// the E4M3 scale (2^(e-7) (1 + m/8), m 2^-9).  Magnitude bits 0x7F are NaN.
+// E4M3 -> FP32, exact, through the hardware E4M3 -> FP16 conversion: every
+// E4M3 value (magnitudes 2^-9 .. 448) is an FP16 normal or zero, and NaN
+// stays NaN.
 __device__ __forceinline__ float to_acc(f8e4m3 v) {
-  const unsigned mag = v.b & 0x7Fu;
-  float f = __uint_as_float(mag << 20) * __uint_as_float((127u + 120u) << 23);  // * 2^120
-  f = mag == 0x7Fu ? __uint_as_float(0x7FC00000u) : f;
-  return __uint_as_float(__float_as_uint(f) | (static_cast<unsigned>(v.b & 0x80u) << 24));
+  return __half2float(__half(__nv_cvt_fp8_to_halfraw(static_cast<__nv_fp8_storage_t>(v.b), __NV_E4M3)));
 }
 
 // Running dot product of a thread.  FP64 operands: FP64 FMA.  FP32 operands
