@@ -1021,6 +1021,21 @@ def main():
     if not torch.equal(torch.from_numpy(hy[(e2e_steps - 1) % 2].numpy()).to(dev), dy[(e2e_steps - 1) % 2]):
         raise RuntimeError("e2e: downloaded y differs from the device result")
     e2e_value = world * b_da / t_e2e / 1e9
+    # the host link that bounds the end-to-end leg: one pinned copy of the
+    # step's x up and of its y down, each alone (best of 5, CUDA events)
+    def copy_gbs(dst, src):
+        best = 1e30
+        for _ in range(5):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dst.copy_(src, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            best = min(best, a.elapsed_time(b) * 1e-3)
+        return src.numel() * src.element_size() / best / 1e9
+    h2d_gbs = copy_gbs(dx[0], hx[0])
+    d2h_gbs = copy_gbs(hy[0], dy[0])
     clk.__exit__(None, None, None)
 
     peaks, peak_kind = measured_peaks()
@@ -1065,7 +1080,9 @@ def main():
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n, "us_per_step": round(t_e2e * 1e6, 2),
                 "pipelined": f"upload / SpMV / download of consecutive steps overlap; each copy "
-                             f"split into {args.e2e_parts} parts on their own streams"},
+                             f"split into {args.e2e_parts} parts on their own streams",
+                "link_h2d_gbs": round(h2d_gbs, 1), "link_d2h_gbs": round(d2h_gbs, 1),
+                "link_bound_us_per_step": round(max(8 * n / h2d_gbs, 8 * n / d2h_gbs) / 1e3, 2)},
         "gpu_launches": args.steps,
         "timing": f"one CUDA-event window over the {args.steps} steps (value, ms_per_step); "
                   f"then {reps} steps each timed by its own event pair (roofline.per_step_*)",

@@ -157,6 +157,20 @@ int damn_validate_csr(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *
                       const int32_t *col, int64_t *h_bad_rows, int64_t *h_bad_cols,
                       void *workspace, size_t ws_bytes, void *stream);
 
+/* The same checks for a DA-CSR matrix (off int16 when off_bits == 16, int8
+ * when 8): rowptr[0] == 0, rowptr[nrows] == nnz, rowptr non-decreasing, and
+ * every stored entry of row r addresses a column r + off inside [0, ncols)
+ * (the shifted view of Listing 2 is only dereferenced in range: Section 4,
+ * Remark 3).  The SpMV kernels clamp their x accesses to [0, ncols) instead
+ * of checking, so a matrix that fails here gives wrong results, not memory
+ * faults.  *h_bad_rows / *h_bad_cols as for damn_validate_csr (h_bad_cols
+ * counts entries whose r + off is out of range).  Uses the workspace of
+ * damn_validate_csr_workspace_size().  Synchronises stream.  Returns
+ * DAMN_ERR_INVALID_ARG when either count is non-zero. */
+int damn_validate_dacsr(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                        const void *off, int32_t off_bits, int64_t *h_bad_rows,
+                        int64_t *h_bad_cols, void *workspace, size_t ws_bytes, void *stream);
+
 /* Round-to-nearest-even conversion of n values: FP64 -> FP32, BF16 or FP8
  * E4M3 (one rounding step, no double rounding through FP32), or FP32 -> BF16
  * or E4M3.  E4M3 has no infinity: a value beyond 464 (rounding past the

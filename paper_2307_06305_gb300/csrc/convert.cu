@@ -280,6 +280,78 @@ extern "C" int damn_validate_csr(int32_t nrows, int32_t ncols, int64_t nnz, cons
   return DAMN_OK;
 }
 
+// DA-CSR validation: a block of kRowsPerBlock rows stages its row pointers,
+// counts decreasing row pointers, and checks r + off in [0, ncols) for its
+// entries (the entry range clamped to [0, nnz), so a broken rowptr cannot
+// make it read outside off).
+template <typename OffT>
+__global__ void __launch_bounds__(kConvThreads)
+k_validate_dacsr(int nrows, int ncols, long long nnz, const int *__restrict__ rowptr,
+                 const OffT *__restrict__ off, ValidateAccum *acc) {
+  __shared__ int rp[kRowsPerBlock + 1];
+  const int r0 = blockIdx.x * kRowsPerBlock;
+  const int nr = min(kRowsPerBlock, nrows - r0);
+  for (int i = threadIdx.x; i <= nr; i += kConvThreads) rp[i] = rowptr[r0 + i];
+  __syncthreads();
+  unsigned long long br = 0, bc = 0;
+  for (int i = threadIdx.x; i < nr; i += kConvThreads) br += rp[i] > rp[i + 1] ? 1 : 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    br += (rowptr[0] != 0 ? 1 : 0) + ((long long)rowptr[nrows] != nnz ? 1 : 0);
+  const long long k0 = max(0LL, min((long long)rp[0], nnz));
+  const long long k1 = max(k0, min((long long)rp[nr], nnz));
+  for (long long k = k0 + threadIdx.x; k < k1; k += kConvThreads) {
+    const int lr = row_of(rp, nr, static_cast<int>(k));
+    const long long c = (long long)r0 + lr + static_cast<long long>(off[k]);
+    bc += (c < 0 || c >= ncols) ? 1 : 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    br += __shfl_xor_sync(0xffffffffu, br, o);
+    bc += __shfl_xor_sync(0xffffffffu, bc, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (br) atomicAdd(&acc->bad_rows, br);
+    if (bc) atomicAdd(&acc->bad_cols, bc);
+  }
+}
+
+extern "C" int damn_validate_dacsr(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t *rowptr,
+                                   const void *off, int32_t off_bits, int64_t *h_bad_rows,
+                                   int64_t *h_bad_cols, void *workspace, size_t ws_bytes,
+                                   void *stream) {
+  if (nrows < 0 || ncols < 0 || nnz < 0 || nnz > INT_MAX)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_validate_dacsr: bad sizes");
+  if (off_bits != 16 && off_bits != 8)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_validate_dacsr: off_bits must be 16 or 8");
+  if (!rowptr || (nnz > 0 && !off) || !h_bad_rows || !h_bad_cols)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_validate_dacsr: NULL pointer");
+  if (!workspace || ws_bytes < damn_validate_csr_workspace_size() || !aligned16(workspace))
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_validate_dacsr: workspace too small or misaligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ValidateAccum *acc = static_cast<ValidateAccum *>(workspace);
+  DAMN_CUDA(cudaMemsetAsync(acc, 0, sizeof(ValidateAccum), s));
+  const int blocks = (nrows + kRowsPerBlock - 1) / kRowsPerBlock;
+  if (blocks > 0) {
+    if (off_bits == 16)
+      k_validate_dacsr<int16_t><<<blocks, kConvThreads, 0, s>>>(
+          nrows, ncols, nnz, rowptr, static_cast<const int16_t *>(off), acc);
+    else
+      k_validate_dacsr<int8_t><<<blocks, kConvThreads, 0, s>>>(
+          nrows, ncols, nnz, rowptr, static_cast<const int8_t *>(off), acc);
+    DAMN_CHECK_LAUNCH("k_validate_dacsr");
+  }
+  ValidateAccum h{};
+  DAMN_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+  DAMN_CUDA(cudaStreamSynchronize(s));
+  if (nrows == 0) h.bad_rows = nnz != 0 ? 1 : 0;  // no block ran: rowptr[0] == nnz must be 0
+  *h_bad_rows = static_cast<int64_t>(h.bad_rows);
+  *h_bad_cols = static_cast<int64_t>(h.bad_cols);
+  if (h.bad_rows || h.bad_cols)
+    return set_error(DAMN_ERR_INVALID_ARG,
+                     "damn_validate_dacsr: %llu bad row pointers, %llu entries with r + off outside [0, %d)",
+                     h.bad_rows, h.bad_cols, ncols);
+  return DAMN_OK;
+}
+
 extern "C" int damn_cast_values(int64_t n, const void *src, int src_dtype, void *dst, int dst_dtype,
                                 void *stream) {
   if (n < 0) return set_error(DAMN_ERR_INVALID_ARG, "damn_cast_values: n < 0");

@@ -110,6 +110,8 @@ _sig("damn_csr_to_dacsr8", ctypes.c_int,
 _sig("damn_csr_to_dacsr_noalloc", ctypes.c_int,
      [I32, I32, I64, P, P, P, ctypes.POINTER(damn_fit_info), P])
 _sig("damn_validate_csr_workspace_size", SZ, [])
+_sig("damn_validate_dacsr", ctypes.c_int,
+     [I32, I32, I64, P, P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64), P, SZ, P])
 _sig("damn_validate_csr", ctypes.c_int,
      [I32, I32, I64, P, P, ctypes.POINTER(I64), ctypes.POINTER(I64), P, SZ, P])
 _sig("damn_cast_values", ctypes.c_int, [I64, P, ctypes.c_int, P, ctypes.c_int, P])
@@ -289,6 +291,20 @@ def damn_validate_csr(rowptr, col, ncols: int, stream=None):
                                 ctypes.byref(br), ctypes.byref(bc), _ptr(ws), ws.numel(),
                                 _stream(stream))
     _check(rc, "damn_validate_csr", allow=(DAMN_ERR_INVALID_ARG,))
+    return int(br.value), int(bc.value)
+
+
+def damn_validate_dacsr(rowptr, off, ncols: int, stream=None):
+    """(bad row pointers, entries with r + off outside [0, ncols)) of a
+    DA-CSR-16 (int16 off) or DA-CSR-8 (int8 off) matrix."""
+    nrows = rowptr.numel() - 1
+    ws = _workspace(_lib.damn_validate_csr_workspace_size(), rowptr.device)
+    br, bc = I64(0), I64(0)
+    bits = 8 if off.dtype == torch.int8 else 16
+    rc = _lib.damn_validate_dacsr(nrows, int(ncols), off.numel(), _ptr(rowptr), _ptr(off), bits,
+                                  ctypes.byref(br), ctypes.byref(bc), _ptr(ws), ws.numel(),
+                                  _stream(stream))
+    _check(rc, "damn_validate_dacsr", allow=(DAMN_ERR_INVALID_ARG,))
     return int(br.value), int(bc.value)
 
 

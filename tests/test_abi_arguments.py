@@ -57,6 +57,12 @@ def _cases(D):
                                                 fi(), N)),
         ("damn_validate_csr", bad, "bad sizes",
          lambda: F("damn_validate_csr")(-1, 4, 0, A16, A16, i64(), i64(), A16, 1 << 20, N)),
+        ("damn_validate_dacsr", bad, "bad sizes",
+         lambda: F("damn_validate_dacsr")(-1, 4, 0, A16, A16, 16, i64(), i64(), A16, 1 << 20, N)),
+        ("damn_validate_dacsr", bad, "off_bits",
+         lambda: F("damn_validate_dacsr")(4, 4, 4, A16, A16, 32, i64(), i64(), A16, 1 << 20, N)),
+        ("damn_validate_dacsr", bad, "workspace",
+         lambda: F("damn_validate_dacsr")(4, 4, 4, A16, A16, 16, i64(), i64(), A16, 0, N)),
         ("damn_cast_values", uns, "dtype",
          lambda: F("damn_cast_values")(10, A16, 0, A16, 0, N)),
         ("damn_cast_values", bad, "n < 0",

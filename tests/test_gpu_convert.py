@@ -113,6 +113,36 @@ def test_validate_csr(D, cuda_dev):
     assert br >= 1 and bc == 2
 
 
+def test_validate_dacsr(D, cuda_dev):
+    """r + off inside [0, ncols) for every entry, for int16 and int8 offsets;
+    out-of-range addresses and broken row pointers are counted, not read."""
+    n = 3000
+    rp, col, _ = W.random_banded(n, 50, np.random.default_rng(19))
+    off = OD.translate(n, rp, col)
+    t_rp = _to(cuda_dev, rp)[0]
+    assert D.damn_validate_dacsr(t_rp, _to(cuda_dev, off.astype(np.int16))[0], n) == (0, 0)
+    rp8, col8, _ = W.random_banded(n, 100, np.random.default_rng(20))
+    off8 = OD.translate(n, rp8, col8)
+    assert np.abs(off8).max() <= 127
+    assert D.damn_validate_dacsr(_to(cuda_dev, rp8)[0], _to(cuda_dev, off8.astype(np.int8))[0],
+                                 n) == (0, 0)
+    bad = off.copy()
+    bad[0] = -5                 # row 0: column -5
+    bad[-1] = 10               # last row: column n + 9
+    bad[len(bad) // 2] = 32767  # a middle row: far past ncols
+    assert D.damn_validate_dacsr(t_rp, _to(cuda_dev, bad.astype(np.int16))[0], n) == (0, 3)
+    # a narrower matrix: every entry with r + off >= ncols counts
+    nc = 2000
+    want = int(np.count_nonzero(OD.entry_rows(n, rp) + off >= nc))
+    assert D.damn_validate_dacsr(t_rp, _to(cuda_dev, off.astype(np.int16))[0], nc)[1] == want
+    # broken row pointers: counted; the entry range stays inside off
+    brp = rp.copy()
+    brp[100] = brp[101] + 7
+    brp[-1] = brp[-1] + 1000
+    br, _ = D.damn_validate_dacsr(_to(cuda_dev, brp)[0], _to(cuda_dev, off.astype(np.int16))[0], n)
+    assert br >= 2
+
+
 def test_cast_values(D, cuda_dev):
     rng = np.random.default_rng(4)
     v = np.concatenate([rng.standard_normal(100000) * 10.0 ** rng.integers(-40, 40, 100000),
