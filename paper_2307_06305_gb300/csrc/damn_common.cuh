@@ -131,6 +131,8 @@ __device__ __forceinline__ bool mbar_try_wait_suspend(uint32_t addr, uint32_t pa
 // Waits for the phase with the given parity to complete, for at most
 // timeout_ns.  On timeout records DAMN_ERR_TIMEOUT in *status and returns
 // false.
+// The clock is read once per 16 tries (each try may suspend the thread up to
+// the hint), so that a waiting warp spends few issue slots.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status,
                                                   uint64_t timeout_ns) {
   const uint32_t a = smem_addr(bar);
@@ -138,7 +140,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   const uint64_t t0 = global_timer_ns();
 #pragma unroll 1
   while (true) {
-    if (mbar_try_wait_suspend(a, parity, 100000u)) return true;
+#pragma unroll 1
+    for (int i = 0; i < 16; ++i)
+      if (mbar_try_wait_suspend(a, parity, 100000u)) return true;
     if (global_timer_ns() - t0 > timeout_ns) {
       if (status) atomicExch(status, DAMN_ERR_TIMEOUT);
       return false;
