@@ -220,7 +220,7 @@ def run_reference(args, rank, world):
 
 PROFILE_CASES = ("stencil27_160_rows_long", "batch512_f64_k1", "laplace3d_128",
                  "laplace3d_128_values", "cg_160_f64", "cg_ir_160_f32", "cg_ir_160_bf16",
-                 "banded_<n>_h<h>_<tiling>_<fmt>")
+                 "banded_<n>_h<h>_<tiling>_<fmt>", "batch512_<f64|f32>_k<k>_<streamed|passes>[_e<E>]")
 
 
 def profile_case(name):
@@ -230,6 +230,11 @@ def profile_case(name):
     if name in PROFILE_CASES[:7]:
         return name
     parts = name.split("_")
+    if (len(parts) in (4, 5) and parts[0] == "batch512" and parts[1] in ("f64", "f32")
+            and parts[2][:1] == "k" and parts[2][1:].isdigit() and 1 <= int(parts[2][1:]) <= 64
+            and parts[3] in ("streamed", "passes")
+            and (len(parts) == 4 or parts[4] in ("e1", "e2", "e4", "e8"))):
+        return name
     tiling = "_".join(parts[3:-1])
     ok = (len(parts) >= 5 and parts[0] == "banded" and parts[2].startswith("h")
           and (tiling == "auto" or tiling in TILING_NAMES) and parts[-1] in ("da16", "csr32"))
@@ -247,7 +252,11 @@ def run_case(args):
     (every k_spmv launch of the run).
     batch512_f64_k1: the 512 random banded matrices converted to DA-CSR-16,
     k = 1 FP64 right-hand sides, a batch plan without autotuning, then
-    --steps direct launches of the batched kernel."""
+    --steps direct launches of the batched kernel.
+    batch512_<f64|f32>_k<k>_<streamed|passes>[_e<E>]: the same with k
+    right-hand sides of that type and the plan pinned to streamed rows (items
+    of 1024 rows) or fixed passes (items of 256 rows), E entry lanes per row
+    (default: the plan's choice from nnz / nrows)."""
     import torch
     import workloads as W
     from paper_2307_06305_gb300 import damn as D
@@ -334,16 +343,23 @@ def run_case(args):
         for _ in range(args.steps):
             D.damn_spmv_dacsr16(t_rp, off, t_val, x, y, plan=plan)
     else:
+        parts = args.case.split("_")
+        dt = torch.float64 if parts[1] == "f64" else torch.float32
+        k = int(parts[2][1:])
         gen = torch.Generator(device=dev)
         gen.manual_seed(W.seed_for(5, 1))
         mats = []
         for n, rp, col, val in W.batch_banded(512):
             t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
             off, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
-            X = torch.rand((n, 1), generator=gen, device=dev, dtype=torch.float64) * 2 - 1
-            Y = torch.empty((n, 1), dtype=torch.float64, device=dev)
-            mats.append((t_rp, off, torch.from_numpy(val).to(dev), X, Y))
-        plan = D.BatchPlan(mats, 1, torch.float64, autotune=False)
+            X = torch.rand((n, k), generator=gen, device=dev, dtype=dt) * 2 - 1
+            Y = torch.empty((n, k), dtype=dt, device=dev)
+            mats.append((t_rp, off, torch.from_numpy(val).to(dev).to(dt), X, Y))
+        plan = D.BatchPlan(mats, k, dt, autotune=False)
+        if len(parts) >= 4:
+            E = int(parts[4][1:]) if len(parts) == 5 else plan.describe()["entry_lanes"]
+            streamed = parts[3] == "streamed"
+            plan.set_shape(streamed, 1024 if streamed else 256, E, 256)
         for _ in range(args.steps):
             plan.launch()
     torch.cuda.synchronize()
@@ -567,7 +583,7 @@ def section_batched(D, torch, dev, reps):
                         "gflops": round(flops / t_g / 1e9, 1), "bytes": nbytes,
                         "tuned": {"rows_per_item": desc["tile_items"], "threads": desc["threads"],
                                   "entry_lanes": desc["entry_lanes"],
-                                  "grid": desc["grid"]}}
+                                  "streamed": desc["streamed"], "grid": desc["grid"]}}
             plan.close()
             del g, mats, plan
         del vals

@@ -475,19 +475,39 @@ typedef struct damn_batch_plan damn_batch_plan;
 
 typedef struct {
   int32_t count, k, dtype, ntiles, grid, threads, tile_items, graph_ready;
-  int32_t entry_lanes;     /* lanes splitting each row's entries (summation shape) */
-  int32_t reserved;
+  int32_t entry_lanes;     /* E: lanes splitting each row's entries */
+  int32_t streamed;        /* 1: row groups take the next row as they finish */
   double tune_ms;          /* best time measured by the autotuner (0 if none) */
 } damn_batch_desc;
 
 /* Builds the work list of a batch of independent DA-CSR-16 products
- * Y_m = A_m X_m (host descriptors, device data).  autotune != 0 times the
- * candidate tilings on the real operands (Y is overwritten) and keeps the
- * fastest, then captures the persistent launch in a CUDA graph.
- * Synchronises stream.  The plan owns device memory until destroyed. */
+ * Y_m = A_m X_m (host descriptors, device data): items of rows_per_item
+ * consecutive rows of one matrix, one warp per item.  Each row is computed by
+ * a row group of L * E lanes (L = the largest power of two <= min(k, 32)
+ * column lanes, E entry lanes; Section 4's shifted-x row loop applied to
+ * every column of X; the E partial sums added by a fixed butterfly), so
+ * results depend only on (k, E).  Two schedules of the row groups:
+ *   fixed passes: the warp's 32 / (L E) groups take 32 / (L E) consecutive
+ *     rows at a time and the pass lasts as long as its longest row;
+ *   streamed: a group that has finished its row takes the item's next row at
+ *     once (rows dealt in order), so the warp's steps stay nearly full.
+ * Every row is computed and written exactly once; an empty row gets 0.
+ * autotune != 0 times the candidate shapes (E, schedule, rows per item,
+ * threads) on the real operands (Y is overwritten) and keeps the fastest; the
+ * default is fixed passes with E from nnz / nrows and items of 256 rows.  Then
+ * the persistent launch is captured in a CUDA graph.  Synchronises stream.
+ * The plan owns device memory until destroyed. */
 int damn_batch_plan_create(int32_t count, const damn_mat_desc *h_descs, int32_t k, int dtype,
                            int autotune, void *stream, damn_batch_plan **out);
 int damn_batch_plan_describe(const damn_batch_plan *plan, damn_batch_desc *h_desc);
+
+/* Sets the launch shape of a batch plan and captures its graph again:
+ * streamed != 0 for streamed rows, else fixed passes; entry_lanes E a power
+ * of two <= 8 with L * E <= 32; rows_per_item in [1, 1024]; threads per block
+ * 32, 64, 128 or 256.  DAMN_ERR_INVALID_ARG for anything else (the plan is
+ * then unchanged).  Synchronises stream before the change. */
+int damn_batch_plan_set_shape(damn_batch_plan *plan, int32_t streamed, int32_t rows_per_item,
+                              int32_t entry_lanes, int32_t threads, void *stream);
 int damn_batch_plan_destroy(damn_batch_plan *plan);
 
 /* One persistent launch computing every Y_m of the batch. */

@@ -126,6 +126,105 @@ __global__ void k_spmm_single(DevDesc d, int k) {
     spmm_row<T, L, J, E>(d, static_cast<int>(base + grp), base + grp < d.nrows, k, li, ei);
 }
 
+// Row-streaming batched kernel: the same row groups and the same per-row
+// arithmetic as k_spmm_batched (so the same bits for the same (k, E)), but a
+// group that has finished its row takes the item's next row at once instead
+// of waiting for the longest row of the warp's pass.  The warp steps U
+// entries per entry lane at a time; after each step the groups whose row
+// ended add their entry lanes' sums (butterfly), write the row and are dealt
+// the next rows in order (a ballot over the finished groups).  So a warp's
+// FMA steps stay nearly full whatever the mix of row lengths; an empty row
+// costs one step.  Groups of one or two lanes step 8 entries per lane (more
+// loads in flight per lane, where each lane gathers from its own row), wider
+// groups 4.
+template <typename T, int L, int J, int E>
+__global__ void k_spmm_streamed(const DevDesc *descs, const int2 *items, int nitems, int k,
+                                int rows_per_item) {
+  constexpr int G = L * E, R = 32 / G, U = G <= 2 ? 8 : 4;
+  const int lane = threadIdx.x & 31, grp = lane / G, li = lane % L, ei = (lane % G) / L;
+  const bool leader = (lane % G) == 0;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long it = warp; it < nitems; it += nwarps) {
+    const int2 item = items[it];
+    const DevDesc d = descs[item.x];
+    const int r0 = item.y, nr = min(rows_per_item, d.nrows - r0);
+    const T *val = static_cast<const T *>(d.val);
+    const T *X = static_cast<const T *>(d.X);
+    T *Y = static_cast<T *>(d.Y);
+    const unsigned ncols = static_cast<unsigned>(d.ncols);
+    int row = grp, next = R, pos = 0, end = 0;
+    if (row < nr) {
+      pos = __ldg(d.rowptr + r0 + row);
+      end = __ldg(d.rowptr + r0 + row + 1);
+    }
+    T acc[J];
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) acc[jj] = T(0);
+    while (__any_sync(0xffffffffu, row < nr)) {
+      const bool active = row < nr;
+      T v[U];
+      unsigned c[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = pos + ei + u * E;
+        v[u] = T(0);
+        c[u] = 0;
+        if (active && q < end) {
+          v[u] = __ldg(val + q);
+          // a column outside [0, ncols) (an invalid offset) reads a valid row
+          c[u] = min(static_cast<unsigned>(r0 + row + static_cast<int>(__ldg(d.off + q))),
+                     ncols - 1u);
+        }
+      }
+      T xv[U][J];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) {
+          const int j = li + jj * L;
+          xv[u][jj] = (active && pos + ei + u * E < end && j < k) ? __ldg(X + (size_t)c[u] * k + j)
+                                                                  : T(0);
+        }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (active && pos + ei + u * E < end)
+#pragma unroll
+          for (int jj = 0; jj < J; ++jj) acc[jj] = fma_acc(v[u], xv[u][jj], acc[jj]);
+      pos += U * E;
+      const bool done = active && pos >= end;
+      if (__any_sync(0xffffffffu, done)) {
+        T tot[J];
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) tot[jj] = acc[jj];
+#pragma unroll
+        for (int o = L; o < G; o <<= 1)
+#pragma unroll
+          for (int jj = 0; jj < J; ++jj) tot[jj] += __shfl_xor_sync(0xffffffffu, tot[jj], o);
+        const unsigned dm = __ballot_sync(0xffffffffu, done && leader);
+        if (done) {
+          if (ei == 0) {
+#pragma unroll
+            for (int jj = 0; jj < J; ++jj) {
+              const int j = li + jj * L;
+              if (j < k) Y[(size_t)(r0 + row) * k + j] = tot[jj];
+            }
+          }
+#pragma unroll
+          for (int jj = 0; jj < J; ++jj) acc[jj] = T(0);
+          // this group's rank among the finished groups (its leader's bit)
+          row = next + __popc(dm & ((1u << (grp * G)) - 1u));
+          if (row < nr) {
+            pos = __ldg(d.rowptr + r0 + row);
+            end = __ldg(d.rowptr + r0 + row + 1);
+          }
+        }
+        next += __popc(dm);
+      }
+    }
+  }
+}
+
 int lanes_for(int k) {
   int L = 1;
   while (L * 2 <= std::min(k, 32)) L *= 2;
@@ -219,10 +318,48 @@ int launch_batched(const DevDesc *descs, const int2 *items, int nitems, int k, i
   }
 }
 
+template <typename T, int L, int E>
+int launch_streamed_le(const DevDesc *descs, const int2 *items, int nitems, int k, int rpi,
+                       int blocks, int threads, cudaStream_t s) {
+  if ((k + L - 1) / L <= 1)
+    k_spmm_streamed<T, L, 1, E><<<blocks, threads, 0, s>>>(descs, items, nitems, k, rpi);
+  else
+    k_spmm_streamed<T, L, 2, E><<<blocks, threads, 0, s>>>(descs, items, nitems, k, rpi);
+  DAMN_CHECK_LAUNCH("k_spmm_streamed");
+  return DAMN_OK;
+}
+
+template <typename T, int L>
+int launch_streamed_l(const DevDesc *descs, const int2 *items, int nitems, int k, int rpi, int E,
+                      int blocks, int threads, cudaStream_t s) {
+  if constexpr (L <= 16)
+    if (E >= 2) {
+      if constexpr (L <= 4)
+        if (E >= 8) return launch_streamed_le<T, L, 8>(descs, items, nitems, k, rpi, blocks, threads, s);
+      if constexpr (L <= 8)
+        if (E >= 4) return launch_streamed_le<T, L, 4>(descs, items, nitems, k, rpi, blocks, threads, s);
+      return launch_streamed_le<T, L, 2>(descs, items, nitems, k, rpi, blocks, threads, s);
+    }
+  return launch_streamed_le<T, L, 1>(descs, items, nitems, k, rpi, blocks, threads, s);
+}
+
+template <typename T>
+int launch_streamed(const DevDesc *descs, const int2 *items, int nitems, int k, int rpi, int E,
+                    int blocks, int threads, cudaStream_t s) {
+  switch (lanes_for(k)) {
+    case 1: return launch_streamed_l<T, 1>(descs, items, nitems, k, rpi, E, blocks, threads, s);
+    case 2: return launch_streamed_l<T, 2>(descs, items, nitems, k, rpi, E, blocks, threads, s);
+    case 4: return launch_streamed_l<T, 4>(descs, items, nitems, k, rpi, E, blocks, threads, s);
+    case 8: return launch_streamed_l<T, 8>(descs, items, nitems, k, rpi, E, blocks, threads, s);
+    case 16: return launch_streamed_l<T, 16>(descs, items, nitems, k, rpi, E, blocks, threads, s);
+    default: return launch_streamed_l<T, 32>(descs, items, nitems, k, rpi, E, blocks, threads, s);
+  }
+}
+
 bool desc_ok(const damn_mat_desc &m) {
   if (m.nrows < 0 || m.ncols < 0 || m.nnz < 0 || m.nnz > INT_MAX) return false;
   if (m.nrows > 0 && (!m.rowptr || !m.Y)) return false;
-  if (m.nnz > 0 && (!m.off || !m.val || !m.X)) return false;
+  if (m.nnz > 0 && (!m.off || !m.val || !m.X || m.ncols == 0)) return false;
   return true;
 }
 
@@ -231,12 +368,15 @@ bool desc_ok(const damn_mat_desc &m) {
 
 using namespace damn;
 
+constexpr int kMaxRowsPerItem = 1024;
+
 struct damn_batch_plan {
   int count, k, dtype;
   DevDesc *d_descs;
   int2 *d_items;
   int nitems;
   int rows_per_item;
+  int streamed;            // 1: row groups take the next row as they finish
   int entry_lanes;         // E: lanes splitting each row's entries
   int threads, blocks;
   std::vector<int> nrows;  // per matrix, to rebuild items
@@ -259,8 +399,48 @@ static int batch_build_items(damn_batch_plan *pl, int rpi) {
   return DAMN_OK;
 }
 
+// Persistent grid: one warp per item, at most 16 blocks per SM.
+static void batch_set_grid(damn_batch_plan *pl) {
+  const int wpb = pl->threads / 32;
+  pl->blocks = std::max(1, std::min(16 * sm_count(), (pl->nitems + wpb - 1) / wpb));
+}
+
+static int batch_launch(const damn_batch_plan *pl, cudaStream_t s);
+
+// Captures the persistent launch of the plan's current shape in a CUDA graph
+// (replacing an earlier one).
+static int batch_capture(damn_batch_plan *pl) {
+  if (pl->graph) cudaGraphExecDestroy(pl->graph);
+  pl->graph = nullptr;
+  if (pl->nitems == 0) return DAMN_OK;
+  cudaStream_t cs;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamCreate");
+  cudaGraph_t g = nullptr;
+  int rc = DAMN_OK;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = batch_launch(pl, cs);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  if (e == cudaSuccess && rc == DAMN_OK) e = cudaGraphInstantiate(&pl->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_error(e, "batch plan graph capture");
+  return DAMN_OK;
+}
+
 static int batch_launch(const damn_batch_plan *pl, cudaStream_t s) {
   if (pl->nitems == 0) return DAMN_OK;
+  if (pl->streamed)
+    return pl->dtype == DAMN_F64
+               ? launch_streamed<double>(pl->d_descs, pl->d_items, pl->nitems, pl->k,
+                                         pl->rows_per_item, pl->entry_lanes, pl->blocks,
+                                         pl->threads, s)
+               : launch_streamed<float>(pl->d_descs, pl->d_items, pl->nitems, pl->k,
+                                        pl->rows_per_item, pl->entry_lanes, pl->blocks,
+                                        pl->threads, s);
   if (pl->dtype == DAMN_F64)
     return launch_batched<double>(pl->d_descs, pl->d_items, pl->nitems, pl->k, pl->rows_per_item,
                                   pl->entry_lanes, pl->blocks, pl->threads, s);
@@ -332,73 +512,91 @@ extern "C" int damn_batch_plan_create(int32_t count, const damn_mat_desc *h_desc
                 nullptr, nullptr};
     pl->entry_lanes = entry_lanes_for(avg, L);
   }
+  pl->streamed = 0;
   int rc = batch_build_items(pl, 256);
   if (rc) return fail(rc);
   pl->threads = 256;
-  pl->blocks = std::max(1, std::min(8 * sm_count(), (pl->nitems * 32 + 255) / 256));
+  batch_set_grid(pl);
   if (autotune && pl->nitems > 0) {
-    const int rpis[2] = {64, 256};
-    const int tps[2] = {128, 256};
+    // candidates: every E, row groups in fixed passes over items of 64 or
+    // 256 rows and streamed rows over items of 256 or 1024 rows, 128 or 256
+    // threads per block
+    struct Shape { int streamed, rpi, E, threads; };
+    std::vector<Shape> cand;
+    for (int streamed : {0, 1})
+      for (int rpi : {64, 256})
+        for (int tp : {128, 256})
+          for (int E = 1; E * L <= 32 && E <= 8; E *= 2)
+            cand.push_back({streamed, streamed ? 4 * rpi : rpi, E, tp});
     float best = 1e30f;
-    int best_rpi = 256, best_tp = 256, best_e = pl->entry_lanes;
+    Shape bs = {pl->streamed, pl->rows_per_item, pl->entry_lanes, pl->threads};
     cudaEvent_t e0, e1;
     DAMN_CUDA(cudaEventCreate(&e0));
     DAMN_CUDA(cudaEventCreate(&e1));
-    for (int a = 0; a < 2 && rc == DAMN_OK; ++a) {
-      rc = batch_build_items(pl, rpis[a]);
-      for (int E = 1; E * L <= 32 && E <= 8 && rc == DAMN_OK; E *= 2) {
-        pl->entry_lanes = E;
-        for (int b = 0; b < 2 && rc == DAMN_OK; ++b) {
-          pl->threads = tps[b];
-          const int warps_per_block = pl->threads / 32;
-          pl->blocks = std::max(1, std::min(16 * sm_count(),
-                                            (pl->nitems + warps_per_block - 1) / warps_per_block));
-          rc = batch_launch(pl, s);  // warm
-          float tmin = 1e30f;
-          for (int r = 0; r < 3 && rc == DAMN_OK; ++r) {
-            cudaEventRecord(e0, s);
-            rc = batch_launch(pl, s);
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            tmin = std::min(tmin, ms);
-          }
-          if (tmin < best) { best = tmin; best_rpi = rpis[a]; best_tp = tps[b]; best_e = E; }
-        }
+    for (size_t c = 0; c < cand.size() && rc == DAMN_OK; ++c) {
+      if (cand[c].rpi != pl->rows_per_item) rc = batch_build_items(pl, cand[c].rpi);
+      if (rc) break;
+      pl->streamed = cand[c].streamed;
+      pl->entry_lanes = cand[c].E;
+      pl->threads = cand[c].threads;
+      batch_set_grid(pl);
+      rc = batch_launch(pl, s);  // warm
+      float tmin = 1e30f;
+      for (int r = 0; r < 3 && rc == DAMN_OK; ++r) {
+        cudaEventRecord(e0, s);
+        rc = batch_launch(pl, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        tmin = std::min(tmin, ms);
       }
+      if (tmin < best) { best = tmin; bs = cand[c]; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return fail(rc);
-    rc = batch_build_items(pl, best_rpi);
+    if (bs.rpi != pl->rows_per_item) rc = batch_build_items(pl, bs.rpi);
     if (rc) return fail(rc);
-    pl->entry_lanes = best_e;
-    pl->threads = best_tp;
-    const int wpb = pl->threads / 32;
-    pl->blocks = std::max(1, std::min(16 * sm_count(), (pl->nitems + wpb - 1) / wpb));
+    pl->streamed = bs.streamed;
+    pl->entry_lanes = bs.E;
+    pl->threads = bs.threads;
+    batch_set_grid(pl);
     pl->tune_ms = best;
   }
-  // capture the persistent launch in a graph
-  if (pl->nitems > 0) {
-    cudaStream_t cs;
-    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return fail(cuda_error(e, "cudaStreamCreate"));
-    cudaGraph_t g = nullptr;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      rc = batch_launch(pl, cs);
-      e = cudaStreamEndCapture(cs, &g);
-    }
-    if (e == cudaSuccess && rc == DAMN_OK) e = cudaGraphInstantiate(&pl->graph, g, 0);
-    if (g) cudaGraphDestroy(g);
-    cudaStreamDestroy(cs);
-    if (rc) return fail(rc);
-    if (e != cudaSuccess) return fail(cuda_error(e, "damn_batch_plan_create: graph"));
-  }
+  rc = batch_capture(pl);
+  if (rc) return fail(rc);
   DAMN_CUDA(cudaStreamSynchronize(s));
   *out = pl;
   return DAMN_OK;
+}
+
+extern "C" int damn_batch_plan_set_shape(damn_batch_plan *plan, int32_t streamed,
+                                         int32_t rows_per_item, int32_t entry_lanes,
+                                         int32_t threads, void *stream) {
+  if (!plan) return set_error(DAMN_ERR_INVALID_ARG, "damn_batch_plan_set_shape: plan is NULL");
+  if (rows_per_item < 1 || rows_per_item > kMaxRowsPerItem)
+    return set_error(DAMN_ERR_INVALID_ARG, "damn_batch_plan_set_shape: rows_per_item must be 1..%d",
+                     kMaxRowsPerItem);
+  if (threads != 32 && threads != 64 && threads != 128 && threads != 256)
+    return set_error(DAMN_ERR_INVALID_ARG,
+                     "damn_batch_plan_set_shape: threads must be 32, 64, 128 or 256");
+  const int L = lanes_for(plan->k);
+  if (entry_lanes < 1 || entry_lanes > 8 || (entry_lanes & (entry_lanes - 1)) ||
+      L * entry_lanes > 32)
+    return set_error(DAMN_ERR_INVALID_ARG,
+                     "damn_batch_plan_set_shape: entry_lanes must be a power of two <= 8 with "
+                     "%d * entry_lanes <= 32", L);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DAMN_CUDA(cudaStreamSynchronize(s));  // no launch of the old shape in flight
+  int rc = batch_build_items(plan, rows_per_item);
+  if (rc) return rc;
+  plan->streamed = streamed ? 1 : 0;
+  plan->entry_lanes = entry_lanes;
+  plan->threads = threads;
+  batch_set_grid(plan);
+  plan->tune_ms = 0.0;
+  return batch_capture(plan);
 }
 
 extern "C" int damn_batch_plan_describe(const damn_batch_plan *plan, damn_batch_desc *h) {
@@ -412,7 +610,7 @@ extern "C" int damn_batch_plan_describe(const damn_batch_plan *plan, damn_batch_
   h->tile_items = plan->rows_per_item;
   h->graph_ready = plan->graph ? 1 : 0;
   h->entry_lanes = plan->entry_lanes;
-  h->reserved = 0;
+  h->streamed = plan->streamed;
   h->tune_ms = plan->tune_ms;
   return DAMN_OK;
 }

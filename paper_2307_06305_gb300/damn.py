@@ -88,7 +88,7 @@ class damn_mat_desc(ctypes.Structure):
 class damn_batch_desc(ctypes.Structure):
     _fields_ = [("count", I32), ("k", I32), ("dtype", I32), ("ntiles", I32), ("grid", I32),
                 ("threads", I32), ("tile_items", I32), ("graph_ready", I32),
-                ("entry_lanes", I32), ("reserved", I32), ("tune_ms", F64)]
+                ("entry_lanes", I32), ("streamed", I32), ("tune_ms", F64)]
 
 
 def _sig(name, res, args):
@@ -159,6 +159,7 @@ _opt("damn_spmm_dacsr16", ctypes.c_int, [I32, I32, I64, P, P, P, ctypes.c_int, I
 _opt("damn_batch_plan_create", ctypes.c_int,
      [I32, ctypes.POINTER(damn_mat_desc), I32, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(P)])
 _opt("damn_batch_plan_describe", ctypes.c_int, [P, ctypes.POINTER(damn_batch_desc)])
+_opt("damn_batch_plan_set_shape", ctypes.c_int, [P, I32, I32, I32, I32, P])
 _opt("damn_batch_plan_destroy", ctypes.c_int, [P])
 _opt("damn_spmm_dacsr16_batched", ctypes.c_int, [P, P])
 _opt("damn_batch_graph_launch", ctypes.c_int, [P, P])
@@ -552,6 +553,14 @@ class BatchPlan:
     def graph_launch(self, stream=None):
         _check(_fn("damn_batch_graph_launch")(self.handle, _stream(stream)),
                "damn_batch_graph_launch")
+
+    def set_shape(self, streamed: bool, rows_per_item: int, entry_lanes: int = 1,
+                  threads: int = 256, stream=None):
+        """Pins the launch shape (streamed rows or fixed passes, entry_lanes
+        lanes per row) and captures the graph again."""
+        _check(_fn("damn_batch_plan_set_shape")(self.handle, int(bool(streamed)), int(rows_per_item),
+                                                int(entry_lanes), int(threads), _stream(stream)),
+               "damn_batch_plan_set_shape")
 
     def describe(self) -> dict:
         d = damn_batch_desc()

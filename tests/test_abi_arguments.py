@@ -114,6 +114,8 @@ def _cases(D):
          lambda: F("damn_spmm_dacsr16_batched")(N, N)),
         ("damn_batch_graph_launch", bad, "NULL",
          lambda: F("damn_batch_graph_launch")(N, N)),
+        ("damn_batch_plan_set_shape", bad, "NULL",
+         lambda: F("damn_batch_plan_set_shape")(N, 1, 64, 1, 128, N)),
         # diagnostics
         ("damn_selftest_wait_timeout", bad, "timeout_ns",
          lambda: F("damn_selftest_wait_timeout")(5, N)),
