@@ -58,17 +58,19 @@ __device__ __forceinline__ void spmm_row(const DevDesc &d, int row, bool valid, 
 #pragma unroll
   for (int jj = 0; jj < J; ++jj) acc[jj] = T(0);
   constexpr int U = 4;
+  const unsigned ncols = static_cast<unsigned>(d.ncols);
   for (int q0 = b + ei; q0 < e; q0 += U * E) {
     T v[U];
-    int c[U];
+    unsigned c[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int q = q0 + u * E;
       v[u] = T(0);
-      c[u] = row;
+      c[u] = 0;
       if (q < e) {
         v[u] = __ldg(val + q);
-        c[u] = row + static_cast<int>(__ldg(d.off + q));
+        // a column outside [0, ncols) (an invalid offset) reads a valid row
+        c[u] = min(static_cast<unsigned>(row + static_cast<int>(__ldg(d.off + q))), ncols - 1u);
       }
     }
     T xv[U][J];
