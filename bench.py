@@ -160,22 +160,56 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def cpu_oracle_baseline(rp, off, val, x, budget_s=10.0):
-    """The plain-C Listing 2 oracle (DA-CSR-16, FP64) on all host cores in the
-    affinity mask, repeated whole SpMVs for about budget_s seconds."""
+def _time_repeated(fn, budget_s):
+    """Seconds per call of fn() repeated for about budget_s seconds (one
+    untimed warm-up call first), and the number of timed calls."""
+    fn()
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        fn()
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            return el / reps, reps
+
+
+def cpu_oracle_baseline(rp, col, off, val, x, budget_s=10.0):
+    """The plain-C Listing 2 oracle (FP64) timed on the host: DA-CSR-16 on all
+    cores of the affinity mask (the reported baseline, about budget_s
+    seconds), then DA-CSR-16 on one core and CSR-32 on all cores (about a
+    fifth of budget_s each).  Returns {name: (seconds per SpMV, reps, threads)}."""
     from oracle import c_listing2 as C
     cores = len(os.sched_getaffinity(0))
     n = len(rp) - 1
     y = np.zeros(n)
-    C.spmv_dacsr16(n, rp, off, val, x, out=y, nthreads=cores)  # warm-up
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        C.spmv_dacsr16(n, rp, off, val, x, out=y, nthreads=cores)
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s:
-            break
-    return el / reps, reps, cores
+    out = {}
+    out["dacsr16"] = _time_repeated(
+        lambda: C.spmv_dacsr16(n, rp, off, val, x, out=y, nthreads=cores), budget_s) + (cores,)
+    out["dacsr16_1thread"] = _time_repeated(
+        lambda: C.spmv_dacsr16(n, rp, off, val, x, out=y, nthreads=1), budget_s / 5) + (1,)
+    out["csr32"] = _time_repeated(
+        lambda: C.spmv_csr32(n, rp, col, val, x, out=y, nthreads=cores), budget_s / 5) + (cores,)
+    return out
+
+
+def cpu_oracle_cg_sample(iters=2):
+    """The oracle's FP64 CG (numpy) on the 160^3 27-point system, b = A x*
+    (x* seeded as in the solvers section): seconds per iteration over `iters`
+    iterations after the initial residual, timed as one call."""
+    import workloads as W
+    from oracle import cg as OC
+    from oracle import dacsr as OD
+    from oracle import c_listing2 as C
+    rp, col, val = W.stencil27(160)
+    n = len(rp) - 1
+    off = OD.translate(n, rp, col).astype(np.int16)
+    del col
+    xs = W.uniform_vector(n, W.rng_for(4, 1))
+    b = C.spmv_dacsr16(n, rp, off, val, xs, nthreads=len(os.sched_getaffinity(0)))
+    t0 = time.perf_counter()
+    res = OC.cg(n, rp, off, val, b, rtol=1e-10, max_iter=iters)
+    el = time.perf_counter() - t0
+    return el / max(res.iterations, 1), res.iterations, n, len(val)
 
 
 def build_inputs():
@@ -1121,13 +1155,32 @@ def main():
         raise RuntimeError("device status word reports an error after the sections")
     if rank == 0:
         from oracle import dacsr as OD
-        t_cpu, reps, cores = cpu_oracle_baseline(rp, OD.translate(n, rp, col).astype(np.int16),
-                                                 val, x, args.cpu_budget)
-        line["cpu_baseline"] = {"value": round(b_da / t_cpu / 1e9, 2), "unit": "GB/s",
-                                "cores": cores, "kind": "oracle",
-                                "sample": f"{reps} whole DA-CSR-16 SpMVs of the full workload "
-                                          f"(plain C Listing 2, OpenMP static rows), "
-                                          f"{t_cpu * reps:.1f} s"}
+        cb = cpu_oracle_baseline(rp, col, OD.translate(n, rp, col).astype(np.int16), val, x,
+                                 args.cpu_budget)
+        t_cpu, reps, cores = cb["dacsr16"]
+        b_csr = spmv_bytes(n, nnz, 4, 8, 8)
+        line["cpu_baseline"] = {
+            "value": round(b_da / t_cpu / 1e9, 2), "unit": "GB/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{reps} whole DA-CSR-16 SpMVs of the full workload "
+                      f"(plain C Listing 2, OpenMP static rows), {t_cpu * reps:.1f} s",
+            "dacsr16_1thread": {"gbs": round(b_da / cb["dacsr16_1thread"][0] / 1e9, 2),
+                                "us": round(cb["dacsr16_1thread"][0] * 1e6, 1),
+                                "reps": cb["dacsr16_1thread"][1], "cores": 1},
+            "csr32": {"gbs": round(b_csr / cb["csr32"][0] / 1e9, 2),
+                      "us": round(cb["csr32"][0] * 1e6, 1), "reps": cb["csr32"][1],
+                      "cores": cores}}
+        if args.cpu_budget >= 5:
+            s_it, its, n_cg, nnz_cg = cpu_oracle_cg_sample()
+            gpu_its = line.get("sections", {}).get("solvers", {}).get("cg_f64", {}).get("iterations")
+            cg = {"s_per_iteration": round(s_it, 3), "iterations_timed": its,
+                  "sample": f"the oracle's FP64 CG (numpy, Listing 2 order per row) on the "
+                            f"160^3 27-point system (n={n_cg}, nnz={nnz_cg}), {its} iterations "
+                            f"after the initial residual, timed as one call"}
+            if gpu_its:
+                cg["projected_s_to_1e-10"] = round(s_it * gpu_its, 1)
+                cg["projected_iterations"] = gpu_its
+            line["cpu_baseline"]["cg_f64"] = cg
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
