@@ -811,21 +811,23 @@ def section_banded(D, torch, dev, reps, full=False):
 
 
 def l2_read_gbs(torch, dev, mbytes=48, calls=200):
-    """Device read bandwidth of an L2-resident buffer: a sum over a 48 MB
-    FP64 buffer (L2 holds 126 MB), 200 calls under one graph replay, the
+    """Device read bandwidth of an L2-resident buffer: row sums of a 48 MB
+    FP64 buffer viewed as rows of 4096 values (L2 holds 126 MB; one block
+    per row, so the whole GPU reads), 200 calls under one graph replay, the
     buffer's bytes over the time per call.  A library reduction, so a lower
     bound of what the L2 delivers to a read stream."""
-    buf = torch.rand(mbytes * (1 << 20) // 8, dtype=torch.float64, device=dev)
-    out = torch.empty((), dtype=torch.float64, device=dev)
+    width = 4096
+    buf = torch.rand(mbytes * (1 << 20) // 8 // width, width, dtype=torch.float64, device=dev)
+    out = torch.empty(buf.shape[0], dtype=torch.float64, device=dev)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
-        torch.sum(buf, dim=0, out=out)
+        torch.sum(buf, dim=1, out=out)
     torch.cuda.current_stream().wait_stream(side)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
         for _ in range(calls):
-            torch.sum(buf, dim=0, out=out)
+            torch.sum(buf, dim=1, out=out)
     g.replay()
     _, t = _event_time(torch, g.replay, 5)
     return buf.numel() * 8 / (t / calls) / 1e9
