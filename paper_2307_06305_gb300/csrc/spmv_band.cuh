@@ -49,6 +49,7 @@ constexpr int kBandRing = 4;  // tile flag: x read from the ring
 template <int NT_, int G_, int CAP_NZ_, int CAP_ROWS_, int W_>
 struct BCfg {
   static constexpr int NT = NT_, G = G_, CAP_NZ = CAP_NZ_, CAP_ROWS = CAP_ROWS_, W = W_;
+  static constexpr bool PERM = false;  // no row permutation in the stages
   static constexpr int CH = 8;  // entries of a slice handled per unrolled step
   static_assert((W & (W - 1)) == 0, "ring size must be a power of two");
   static_assert(G * NT / 32 <= 32, "too many consumer warps");
@@ -59,7 +60,9 @@ struct BCfg {
 // rows of a dozen entries, so that a row rarely spans more than two slices
 // and the FP64 adds of slice carries stay few), 2048-entry stages; FP64: an
 // 8192-element ring (64 KB, bands up to a few thousand columns each side);
-// FP32 / BF16 values (FP32 x): a 16384-element ring (64 KB).
+// FP32 / BF16 values (FP32 x): a 16384-element ring (64 KB).  (Stages of 2560
+// entries, tried: no faster for bands up to 1000 wide and much slower for
+// wide bands whose x is gathered from global memory.)
 using CfgBand64 = BCfg<128, 4, 2048, 512, 8192>;
 using CfgBand32 = BCfg<128, 4, 2048, 512, 16384>;
 
@@ -72,6 +75,7 @@ using CfgBand32 = BCfg<128, 4, 2048, 512, 16384>;
 template <int NT_, int G_, int CAP_NZ_, int W_>
 struct RCfg {
   static constexpr int NT = NT_, G = G_, CAP_NZ = CAP_NZ_, CAP_ROWS = NT_, W = W_;
+  static constexpr bool PERM = true;  // the tile's row permutation in each stage
   static constexpr int CH = 16;     // entries loaded ahead per row (even)
   static constexpr int LONG = 128;  // rows longer than this are shared by a warp
   static_assert((W & (W - 1)) == 0, "ring size must be a power of two");
@@ -83,7 +87,7 @@ using CfgSorted32 = RCfg<192, 2, 3584, 8192>;
 struct __align__(16) BandHdr {
   int r0, nr, k0, m;
   int flags, rp_sh, v_sh, i_sh;
-  int kd;          // entries per consumer slice, ceil(m / NT) (at least 1)
+  int kd;          // entries per consumer slice: ceil(m / NT), made odd
   unsigned kdm;    // ceil(2^32 / kd): a / kd as a multiply-high (DivK)
   int pad[2];
 };
@@ -96,7 +100,7 @@ struct BandLayout {
   static constexpr size_t V_BYTES = align_up((C::CAP_NZ + 2 * EV) * sizeof(V), 128);
   static constexpr size_t I_BYTES = align_up((C::CAP_NZ + 2 * EI) * sizeof(I), 128);
   // row permutation of a sorted-rows tile (uint16 per row)
-  static constexpr size_t P_BYTES = align_up((C::CAP_ROWS + 8) * 2, 128);
+  static constexpr size_t P_BYTES = C::PERM ? align_up((C::CAP_ROWS + 8) * 2, 128) : 0;
   static constexpr size_t OFF_V = RP_BYTES, OFF_I = RP_BYTES + V_BYTES,
                           OFF_P = RP_BYTES + V_BYTES + I_BYTES;
   static constexpr size_t STAGE = RP_BYTES + V_BYTES + I_BYTES + P_BYTES;
@@ -154,7 +158,10 @@ __device__ __forceinline__ void band_prepare(const SpmvParams &p, long long t, l
   bi.tails = (rr.tb < r1 + 1) || (!direct && m > 0 && (rv.tb < k1 || ri.tb < k1));
   bi.h0 = make_int4(r0, nr, k0, m);
   {
-    const int kd = m > 0 ? (m + C::NT - 1) / C::NT : 1;
+    // an odd slice length: thread t's loads of entry t kd + u then fall in
+    // distinct shared-memory banks for 8-, 4- and 2-byte elements (an even
+    // kd, 16 say, would put every thread of a warp on one bank)
+    const int kd = m > 0 ? ((m + C::NT - 1) / C::NT) | 1 : 1;
     bi.h2 = make_int4(kd, static_cast<int>(0xFFFFFFFFu / static_cast<unsigned>(kd) + 1u), 0, 0);
   }
   bi.h1 = make_int4(direct ? kTileDirect : 0, static_cast<int>(r0 - rr.a0),
@@ -163,7 +170,8 @@ __device__ __forceinline__ void band_prepare(const SpmvParams &p, long long t, l
   bi.v_a0 = rv.a0; bi.v_bytes = rv.bulk_bytes;
   bi.i_a0 = ri.a0; bi.i_bytes = ri.bulk_bytes;
   // the permutation array is padded to whole tiles: copy whole 16-byte blocks
-  bi.p_bytes = p.perm ? static_cast<uint32_t>(((nr + 7) & ~7) * 2) : 0u;
+  // (stages of a layout without a permutation buffer never receive one)
+  bi.p_bytes = (C::PERM && p.perm) ? static_cast<uint32_t>(((nr + 7) & ~7) * 2) : 0u;
   bi.lo = INT_MAX; bi.hi = INT_MIN; bi.minlo = INT_MAX;
   if (p.colrange && !direct && m > 0) {
     const int2 cr = __ldg(p.colrange + t);
