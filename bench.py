@@ -746,6 +746,8 @@ L2_BYTES = 126e6
 TILING_NAMES = ("slices", "rows", "rows_long", "band", "lanes4", "lanes8", "lanes16",
                 "lanes32", "sorted", "rows_x2")   # DAMN_TILING_* 0 .. 9
 BANDED_TILINGS = (0, 2, 3, 8)  # the tilings timed in the banded section
+# (tiling, x staging) pairs of the banded section: band also without its ring
+BANDED_SHAPES = tuple((t, True) for t in BANDED_TILINGS) + ((3, False),)
 
 
 def section_banded(D, torch, dev, reps, full=False):
@@ -778,10 +780,11 @@ def section_banded(D, torch, dev, reps, full=False):
               "heuristic_tiling": TILING_NAMES[desc["tiling"]],
               "row_efficiency": round(desc["row_efficiency"], 3), "max_row": desc["max_row"],
               "tilings": {}}
-        for tiling in BANDED_TILINGS:
-            tname = TILING_NAMES[tiling]
+        for tiling, xstage in BANDED_SHAPES:
+            tname = TILING_NAMES[tiling] + ("" if xstage else "_xg")
             for pl in plans:
                 pl.set_tiling(tiling)
+                pl.set_x_staging(xstage)
             tt = {"x_staged_tiles_frac": round(plans[0].describe()["x_staged_tiles"]
                                                / max(1, plans[0].describe()["ntiles"]), 3)}
             for fmt, fn, k in (("da16", D.damn_spmv_dacsr16, 2), ("csr32", D.damn_spmv_csr32, 1)):

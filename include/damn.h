@@ -334,8 +334,11 @@ int damn_plan_set_stages(damn_plan *plan, int32_t stages);
  * default) stages each tile's x window in shared memory; on == 0 reads x
  * from global memory (L1 / L2) instead, with the same register-batched row
  * loop -- cheaper per entry when a warp's rows read consecutive x entries at
- * each offset (stencil-like patterns).  Results are bitwise the same either
- * way.  No device work.  The autotuner tries both for rows tilings. */
+ * each offset (stencil-like patterns).  DAMN_TILING_BAND: on == 0 launches
+ * without the x ring (every tile gathers x from L1 / L2), leaving the ring's
+ * 64 KB of shared memory to the L1 cache -- for bands too wide for the ring.
+ * Results are bitwise the same either way.  No device work.  The autotuner
+ * tries both for rows and band tilings. */
 int damn_plan_set_x_staging(damn_plan *plan, int32_t on);
 
 int damn_plan_describe(const damn_plan *plan, damn_plan_desc *h_desc);

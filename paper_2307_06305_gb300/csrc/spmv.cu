@@ -402,7 +402,7 @@ struct damn_plan {
   double row_eff;
   int max_tile_short, max_tile_long;
   int stages_req;         // requested ring depth (0: automatic)
-  int no_xstage;          // rows tilings: read x from global memory, stage no x window
+  int no_xstage;          // rows tilings: stage no x window; band: no x ring (x from L1 / L2)
   int grid, stages;       // geometry of the last launch
 };
 
@@ -498,7 +498,7 @@ static int make_params(const SpmvCall &c, const damn_plan *plan, SpmvParams &p, 
     p.ntiles = plan->ntiles;
     p.bounds = plan->d_bounds;
     p.xseg = (plan->mode >= 2 || (plan->mode == 0 && plan->no_xstage)) ? nullptr : plan->d_xseg;
-    p.colrange = plan->mode == 2 ? plan->d_colrange
+    p.colrange = plan->mode == 2 ? (plan->no_xstage ? nullptr : plan->d_colrange)
                  : plan->mode == 3 ? plan->d_colrange_sorted : nullptr;
     p.perm = plan->mode == 3 ? plan->d_perm : nullptr;
     p.stages_req = plan->stages_req;
@@ -904,8 +904,10 @@ extern "C" int damn_plan_autotune(damn_plan *plan, int format, const void *idx, 
     if (t < 0.97f * best_ms) { best_ms = t; best_st = st; }
   }
   plan->stages_req = rc ? keep_stages : best_st;
-  // 3. rows tilings: x staged in shared memory, or read from L1 / L2
-  if (!rc && plan->mode == 0 && plan->d_xseg) {
+  // 3. rows tilings: x staged in shared memory, or read from L1 / L2; band
+  //    tiling: x through the ring, or gathered from L1 / L2 with the ring's
+  //    shared memory left to the L1 cache
+  if (!rc && ((plan->mode == 0 && plan->d_xseg) || (plan->mode == 2 && plan->d_colrange))) {
     plan->no_xstage = 1;
     float t = 1e30f;
     rc = time_plan(&t);

@@ -490,8 +490,11 @@ __global__ void __launch_bounds__(C::G * C::NT + 32, 1) k_spmv_band(const SpmvPa
   using A = typename AccOf<V>::type;
   using L = BandLayout<V, I, C>;
   extern __shared__ __align__(128) unsigned char smem[];
+  // without column ranges no tile reads x through the ring, and the launch
+  // leaves out its shared memory (the L1 cache gets it)
   A *ring = reinterpret_cast<A *>(smem + (size_t)p.stages * L::STAGE);
-  unsigned char *ctrl = smem + (size_t)p.stages * L::STAGE + L::RING_BYTES;
+  unsigned char *ctrl =
+      smem + (size_t)p.stages * L::STAGE + (p.colrange ? L::RING_BYTES : size_t(0));
   uint64_t *full = reinterpret_cast<uint64_t *>(ctrl + L::C_FULL);
   uint64_t *empty = reinterpret_cast<uint64_t *>(ctrl + L::C_EMPTY);
   BandHdr *hdr = reinterpret_cast<BandHdr *>(ctrl + L::C_HDR);

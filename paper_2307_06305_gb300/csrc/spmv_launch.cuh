@@ -114,20 +114,27 @@ int launch_kernel(SpmvParams p, cudaStream_t s, int *gs_out) {
 template <bool PLAIN, typename V, typename I, class C>
 int launch_band(SpmvParams p, cudaStream_t s, int *gs_out) {
   using L = BandLayout<V, I, C>;
-  static Occ cache[kMaxDev];
+  static Occ cache[2][kMaxDev];
   static std::mutex mu;
+  // no column ranges: no tile reads x through the ring, whose shared memory
+  // is then left to the L1 cache
+  const int ring = p.colrange ? 1 : 0;
+  auto total = [ring](int k) { return L::total(k) - (ring ? size_t(0) : L::RING_BYTES); };
+  // without the ring every x value is gathered through L1: unless a depth is
+  // requested, one stage per consumer group, so that the shared memory saved
+  // goes to the L1 cache rather than to a deeper ring of stages
+  const int req = p.stages_req > 0 ? p.stages_req : (ring ? 0 : C::G);
   int st = 2, occ = 1;
-  int rc = pick_geometry(k_spmv_band<PLAIN, V, I, C>, C::G * C::NT + 32,
-                         [](int k) { return L::total(k); }, 1, p.stages_req, cache, mu, &st, &occ,
-                         C::G);
+  int rc = pick_geometry(k_spmv_band<PLAIN, V, I, C>, C::G * C::NT + 32, total, 1, req,
+                         cache[ring], mu, &st, &occ, C::G);
   if (rc) return rc;
   p.stages = st;
   // one chunk of consecutive tiles per CTA; at least a few tiles per chunk
   const int grid = std::max(1, std::min(occ * sm_count(), (p.ntiles + 3) / 4));
   if (gs_out) { gs_out[0] = grid; gs_out[1] = p.stages; }
   if (p.ntiles == 0) return DAMN_OK;
-  return launch_pdl(k_spmv_band<PLAIN, V, I, C>, grid, C::G * C::NT + 32, L::total(p.stages), s,
-                    p, "k_spmv_band");
+  return launch_pdl(k_spmv_band<PLAIN, V, I, C>, grid, C::G * C::NT + 32, total(p.stages), s, p,
+                    "k_spmv_band");
 }
 
 template <bool PLAIN, typename V, typename I, class C>

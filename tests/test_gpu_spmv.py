@@ -24,7 +24,7 @@ pytestmark = pytest.mark.gpu
 # each tiling pinned (x windows from off); a plan without x windows (x gathered)
 MODES = ["none", "auto", "auto_col", "rows", "rows_long", "slices", "rows_gather", "band",
          "band_col", "band_gather", "lanes4", "lanes8", "lanes16", "lanes32", "sorted",
-         "sorted_col", "sorted_gather", "rows_x2", "rows_xg", "rows_long_xg"]
+         "sorted_col", "sorted_gather", "rows_x2", "rows_xg", "rows_long_xg", "band_xg"]
 
 
 def _t(dev, a):
@@ -65,6 +65,8 @@ def _plan(D, m, mode):
         tiling = D.DAMN_TILING_ROWS
     if mode == "rows_long_xg":
         tiling = D.DAMN_TILING_ROWS_LONG
+    if mode == "band_xg":
+        tiling = D.DAMN_TILING_BAND
     if tiling is not None:
         p.set_tiling(tiling)
     if mode.endswith("_xg"):
