@@ -528,6 +528,11 @@ def section_solvers(D, torch, dev, reps, perturb=False):
     }
     out = {"workload": "stencil27_160^3_cg_to_1e-10" + ("_perturbed_0.01" if perturb else ""),
            "n": n, "nnz": nnz}
+    for name, pl in (("f64", p64), ("f32", p32), ("bf16", p16)):
+        dsc = pl.describe()
+        out.setdefault("plans", {})[name] = {"tiling": TILING_NAMES[dsc["tiling"]],
+                                             "stages": dsc["stages"],
+                                             "x_staging": dsc["x_staging"]}
     # low-precision SpMV error against the FP64 SpMV, per dtype (x = x*)
     y64 = torch.empty(n, dtype=torch.float64, device=dev)
     D.damn_spmv_dacsr16(t_rp, off, t_val, xs, y64, plan=p64)

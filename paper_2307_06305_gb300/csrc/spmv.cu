@@ -31,6 +31,7 @@ static_assert(kBalancedItems / kRowWeight <= CfgSlices::CAP_ROWS, "balanced tile
 static_assert(CfgShort::TILE_ROWS <= CfgShort::CAP_ROWS &&
                   CfgShortNarrow::TILE_ROWS <= CfgShortNarrow::CAP_ROWS &&
                   CfgLong::TILE_ROWS <= CfgLong::CAP_ROWS && 256 <= CfgSlices::CAP_ROWS &&
+                  CfgLongNarrow::TILE_ROWS <= CfgLongNarrow::CAP_ROWS &&
                   CfgShortX2::TILE_ROWS <= CfgShortX2::CAP_ROWS &&
                   CfgShortNarrowX2::TILE_ROWS <= CfgShortNarrowX2::CAP_ROWS,
               "row tiles too tall");
@@ -417,7 +418,11 @@ struct CfgGeom {
 };
 static CfgGeom cfg_geom(int shape, int dtype) {
   switch (shape) {
-    case kShapeLong: return {CfgLong::TILE_ROWS, CfgLong::CAP_NZ, CfgLong::XCAP, CfgLong::NT};
+    case kShapeLong:
+      if (dtype != DAMN_F64)
+        return {CfgLongNarrow::TILE_ROWS, CfgLongNarrow::CAP_NZ, CfgLongNarrow::XCAP,
+                CfgLongNarrow::NT};
+      return {CfgLong::TILE_ROWS, CfgLong::CAP_NZ, CfgLong::XCAP, CfgLong::NT};
     case kShapeSlices: return {0, CfgSlices::CAP_NZ, CfgSlices::XCAP, CfgSlices::NT};
     case kShapeBand:
       return {0, CfgBand64::CAP_NZ, dtype == DAMN_F64 ? CfgBand64::W : CfgBand32::W,

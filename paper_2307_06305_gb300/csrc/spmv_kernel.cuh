@@ -158,6 +158,11 @@ struct KCfg {
 using CfgShort = KCfg<256, 1792, 256, 1280, 3, 1>;
 using CfgShortNarrow = KCfg<256, 3584, 512, 2560, 3, 2>;
 using CfgLong = KCfg<256, 3584, 128, 1536, 2, 1, 2>;
+// Rows mode, long rows, FP32 / BF16 / FP8 values: the same tiles with three
+// CTAs per SM (the narrow stages leave the shared memory for it; at most 72
+// registers per thread), so that more warps hide the shared-memory latency
+// of the narrow kernels, which issue more instructions per byte.
+using CfgLongNarrow = KCfg<256, 3584, 128, 1536, 3, 1, 2>;
 using CfgSlices = KCfg<256, 2048, 512, 1280, 2, 1>;
 // Rows mode with twice the rows per thread of CfgShort / CfgShortNarrow:
 // FP64 values two rows per thread (two independent FMA chains), FP32 / BF16

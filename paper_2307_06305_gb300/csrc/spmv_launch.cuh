@@ -162,16 +162,17 @@ inline bool is_plain(const SpmvParams &p) {
 template <typename V, typename I, class C>
 int launch_cfg(const SpmvParams &p, cudaStream_t s, int *gs) {
   const bool plain = is_plain(p);
-  // one row per lane with every x window of at most 3 segments: one compare
-  // fewer per entry in the column -> slot map
+  // rows without x windows: x read from global memory in the batched path
   if constexpr (C::E <= 2) {
-    // rows without x windows: x read from global memory in the batched path
     if (p.mode == 0 && !p.xseg) {
       if (plain) return launch_kernel<true, V, I, C, 0>(p, s, gs);
       return launch_kernel<false, V, I, C, 0>(p, s, gs);
     }
   }
-  if constexpr (C::E == 1) {
+  // one row per lane (or two lanes per row with narrow values) with every x
+  // window of at most 3 segments: one compare fewer per entry in the column
+  // -> slot map
+  if constexpr (C::E == 1 || (C::E == 2 && sizeof(V) < 8)) {
     if (p.mode == 0 && p.max_nseg <= 3) {
       if (plain) return launch_kernel<true, V, I, C, 3>(p, s, gs);
       return launch_kernel<false, V, I, C, 3>(p, s, gs);
@@ -189,7 +190,11 @@ int launch_types(const SpmvParams &p, int shape, cudaStream_t s, int *gs) {
     case kShapeSorted:
       return is_plain(p) ? launch_sorted<true, V, I, CS>(p, s, gs)
                          : launch_sorted<false, V, I, CS>(p, s, gs);
-    case kShapeLong: return launch_cfg<V, I, CfgLong>(p, s, gs);
+    case kShapeLong:
+      if constexpr (sizeof(V) < 8)
+        return launch_cfg<V, I, CfgLongNarrow>(p, s, gs);
+      else
+        return launch_cfg<V, I, CfgLong>(p, s, gs);
     case kShapeSlices: return launch_cfg<V, I, CfgSlices>(p, s, gs);
     case kShapeBand:
       return is_plain(p) ? launch_band<true, V, I, CB>(p, s, gs)
