@@ -89,3 +89,26 @@ def test_cg_ir_with_quantised_values():
     res = G.cg_ir(n, rp, off, v2, vq, b, rtol=1e-10, inner_rtol=1e-2)
     assert res.converged
     assert np.linalg.norm(b - A @ res.x) <= 1.5e-10 * np.linalg.norm(b)
+
+
+def test_inner_cg_finite_termination_on_a_diagonal_matrix():
+    """CG ends after as many steps as the matrix has distinct eigenvalues
+    (exact arithmetic).  On diag(2, 4, ..., 2, 4) with FP32 vectors the inner
+    solve reaches d = s / diag to FP32 accuracy in two steps, and a third is
+    never needed; a zero right-hand side takes no step."""
+    n = 64
+    rowptr = np.arange(n + 1, dtype=np.int32)
+    off = np.zeros(n, dtype=np.int16)                  # DA-CSR: the diagonal
+    diag = np.where(np.arange(n) % 2 == 0, 2.0, 4.0).astype(np.float32)
+    s = np.random.default_rng(3).uniform(-1, 1, n).astype(np.float32)
+    d, it = G.cg_lowp(n, rowptr, off, diag, s, inner_rtol=1e-6, max_inner=10)
+    assert it == 2
+    assert d.dtype == np.float32
+    np.testing.assert_allclose(d, s / diag, rtol=1e-5, atol=1e-7)
+    d0, it0 = G.cg_lowp(n, rowptr, off, diag, np.zeros(n, dtype=np.float32), max_inner=10)
+    assert it0 == 0 and not d0.any()
+    # one distinct eigenvalue: one step
+    d1, it1 = G.cg_lowp(n, rowptr, off, np.full(n, 2.0, dtype=np.float32), s,
+                        inner_rtol=1e-6, max_inner=10)
+    assert it1 == 1
+    np.testing.assert_allclose(d1, s / 2.0, rtol=1e-6)

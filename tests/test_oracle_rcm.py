@@ -248,3 +248,15 @@ def test_planted_mistakes_are_caught(mistake, monkeypatch):
     wrong = [name for name, n, rp, c, perm in _pinned_cases()
              if np.asarray(order(n, rp, c)).tolist() != perm]
     assert wrong, mistake
+
+
+def test_inverse_permutation():
+    """iperm[perm[i]] = i, by hand and on random permutations (both ways)."""
+    assert R.inverse_permutation([2, 0, 1]).tolist() == [1, 2, 0]
+    assert R.inverse_permutation([0]).tolist() == [0]
+    rng = np.random.default_rng(7)
+    for n in (1, 2, 17, 1000):
+        perm = rng.permutation(n)
+        ip = R.inverse_permutation(perm)
+        assert np.array_equal(ip[perm], np.arange(n))
+        assert np.array_equal(perm[ip], np.arange(n))
