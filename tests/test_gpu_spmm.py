@@ -153,7 +153,7 @@ def _odd_batch(rng):
 
 @pytest.mark.parametrize("shape", [(1, 1, 1, 32), (1, 7, 2, 64), (1, 64, 1, 256), (1, 1024, 4, 128),
                                    (1, 256, 8, 256), (0, 64, 1, 128), (0, 7, 2, 32)])
-@pytest.mark.parametrize("k", [1, 3, 16, 40])
+@pytest.mark.parametrize("k", [1, 3, 16, 40, 64])
 @pytest.mark.parametrize("dt", [torch.float64, torch.float32])
 def test_batched_shapes_exact(D, cuda_dev, shape, k, dt):
     """Every launch shape (streamed rows, fixed passes; entry lanes, rows per
