@@ -254,6 +254,7 @@ def run_reference(args, rank, world):
 
 PROFILE_CASES = ("stencil27_160_rows_long", "batch512_f64_k1", "laplace3d_128",
                  "laplace3d_128_values", "cg_160_f64", "cg_ir_160_f32", "cg_ir_160_bf16",
+                 "laplace3d_128_dacoo16",
                  "banded_<n>_h<h>_<tiling>_<fmt>", "batch512_<f64|f32>_k<k>_<streamed|passes>[_e<E>]")
 
 
@@ -261,7 +262,7 @@ def profile_case(name):
     """argparse type of --case: a fixed case name, or a random banded case
     banded_<n>_h<h>_<tiling>_<fmt> (n like 1e6, tiling auto / rows /
     rows_long / slices, fmt da16 / csr32)."""
-    if name in PROFILE_CASES[:7]:
+    if name in PROFILE_CASES[:8]:
         return name
     parts = name.split("_")
     if (len(parts) in (4, 5) and parts[0] == "batch512" and parts[1] in ("f64", "f32")
@@ -284,6 +285,8 @@ def run_case(args):
     stencil27_160_rows_long: the 160^3 27-point stencil converted to
     DA-CSR-16, a plan pinned to the rows-long tiling, then --steps FP64 SpMVs
     (every k_spmv launch of the run).
+    laplace3d_128_dacoo16: the 128^3 grid as DA-COO-16 (int32 rows, int16
+    offsets), FP64, --steps SpMVs.
     batch512_f64_k1: the 512 random banded matrices converted to DA-CSR-16,
     k = 1 FP64 right-hand sides, a batch plan without autotuning, then
     --steps direct launches of the batched kernel.
@@ -364,6 +367,19 @@ def run_case(args):
         plan = D.Plan(t_rp, nnz, n, torch.float64, idx=off)
         for _ in range(args.steps):
             D.damn_spmv_dacsr16(t_rp, off, t_val, x, y, plan=plan)
+    elif args.case == "laplace3d_128_dacoo16":
+        rp, col, val, xh = build_inputs()
+        n = len(rp) - 1
+        row = np.repeat(np.arange(n, dtype=np.int32), np.diff(rp))
+        t_rp, t_col = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
+        off, _ = D.damn_csr_to_dacsr(t_rp, t_col, n, raise_on_nofit=True)
+        t_row, t_val = torch.from_numpy(row).to(dev), torch.from_numpy(val).to(dev)
+        x = torch.from_numpy(xh).to(dev)
+        y = torch.empty(n, dtype=torch.float64, device=dev)
+        ws = D._workspace(D._fn("damn_coo_workspace_size")(len(col), D._DTYPE_CODE[torch.float64]),
+                          dev)
+        for _ in range(args.steps):
+            D.damn_spmv_dacoo16(n, t_row, off, t_val, x, y, workspace=ws)
     elif args.case == "stencil27_160_rows_long":
         rp, col, val = W.stencil27(160)
         n, nnz = len(rp) - 1, len(col)
