@@ -395,3 +395,28 @@ def test_band_outliers_and_nonsquare(D, cuda_dev):
             got = _run(D, mn, xn, plan=plan)
             _bound_check(mn, xn, got)
             assert np.array_equal(got, _run(D, mn, xn, plan=plan, fmt="csr"))
+
+
+@pytest.mark.parametrize("h", [300, 30000])
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32, torch.bfloat16])
+def test_band_without_ring_same_bits(D, cuda_dev, h, dt):
+    """The band tiling with its x ring and without it (x staging off: every
+    tile gathers x from global memory, the ring's shared memory left to L1)
+    gives the same bits -- the ring only changes where x comes from -- for
+    both index formats, with and without a requested ring depth."""
+    rng = np.random.default_rng(500 + h)
+    n = 40000
+    rp, col, val = W.random_banded(n, h, rng)
+    m = Mat(D, cuda_dev, n, n, rp, col, val, dt)
+    x = W.uniform_vector(n, rng)
+    plan = _plan(D, m, "band")
+    ring = _run(D, m, x, plan=plan)
+    ring_csr = _run(D, m, x, plan=plan, fmt="csr")
+    plan.set_x_staging(False)
+    assert plan.describe()["x_staging"] == 0
+    assert np.array_equal(_run(D, m, x, plan=plan), ring)
+    assert np.array_equal(_run(D, m, x, plan=plan, fmt="csr"), ring_csr)
+    plan.set_stages(8)
+    assert np.array_equal(_run(D, m, x, plan=plan), ring)
+    assert np.array_equal(ring, ring_csr)
+    assert D.damn_device_status() == D.DAMN_OK
