@@ -14,9 +14,13 @@
 // takes 32 / (L * E) rows per pass.
 //
 // Batched launch: the host builds a list of (matrix, first row) work items
-// of rows_per_item rows each; persistent warps take items round-robin.  The
-// plan's autotuner times the (rows_per_item, E, threads) shapes on the real
-// operands and keeps the fastest; the launch is captured in a CUDA graph.
+// of rows_per_item rows each; persistent warps take items round-robin.  A
+// warp's row groups either take the item's rows in fixed passes (a pass
+// lasts as long as its longest row) or are streamed rows (a group whose row
+// ended takes the item's next row at once); both sum a row the same way.
+// The plan's autotuner times the (schedule, rows_per_item, E, threads)
+// shapes on the real operands and keeps the fastest; the launch is captured
+// in a CUDA graph.
 #include <algorithm>
 #include <climits>
 #include <cstring>
