@@ -67,3 +67,22 @@ def test_kernel_source_hash_ignores_comments(tmp_path, monkeypatch):
     assert bench.kernel_source_hash() == h0
     p.write_text(p.read_text() + "static int changed_code = 1;\n")
     assert bench.kernel_source_hash() != h0
+
+
+def test_profile_case_names():
+    """The --case names the committed ncu summaries use are accepted, and
+    malformed ones are refused before any GPU work."""
+    import argparse
+    import pytest
+    ok = ["laplace3d_128", "laplace3d_128_values", "laplace3d_128_dacoo16",
+          "stencil27_160_rows_long", "cg_ir_160_bf16", "batch512_f64_k1",
+          "batch512_f64_k1_streamed_e2", "batch512_f64_k1_passes_e2", "batch512_f32_k16_streamed",
+          "banded_1e6_h1000_band_da16", "banded_1e5_h30000_rows_long_csr32"]
+    for name in ok:
+        assert bench.profile_case(name) == name
+    bad = ["batch512_f64_k0_streamed", "batch512_f64_k65_passes", "batch512_f16_k1_passes",
+           "batch512_f64_k1_streamed_e3", "banded_1e6_h1000_band_da8", "banded_1e6_1000_band_da16",
+           "laplace3d_64"]
+    for name in bad:
+        with pytest.raises(argparse.ArgumentTypeError):
+            bench.profile_case(name)
