@@ -459,7 +459,8 @@ int damn_cg_ir(int32_t n, int64_t nnz, const int32_t *rowptr, const int16_t *off
  * nrows x k (1 <= k <= 64).  dtype F64 (X, Y FP64) or F32 (X, Y FP32).
  * Each row's entries are split over E lanes (E chosen from nnz / nrows, about
  * four entries per lane and pass) whose partial sums are added in a fixed
- * butterfly order; results depend only on (k, E).  nnz > 0 needs ncols >= 1;
+ * butterfly order; results depend only on (k, E).  nnz at most 2^31 - 65
+ * per matrix; nnz > 0 needs ncols >= 1;
  * an entry whose column r + off lies outside [0, ncols) (invalid input, which
  * damn_validate_dacsr reports) reads row ncols - 1 of X instead of memory
  * outside X.  The same holds for the batched launches. */

@@ -362,8 +362,12 @@ int launch_streamed(const DevDesc *descs, const int2 *items, int nitems, int k, 
   }
 }
 
+// Entry positions are int and step past a row's end by up to 32 (U entries
+// for each of the E entry lanes): nnz keeps that headroom below INT_MAX.
+constexpr long long kMaxSpmmNnz = (long long)INT_MAX - 64;
+
 bool desc_ok(const damn_mat_desc &m) {
-  if (m.nrows < 0 || m.ncols < 0 || m.nnz < 0 || m.nnz > INT_MAX) return false;
+  if (m.nrows < 0 || m.ncols < 0 || m.nnz < 0 || m.nnz > kMaxSpmmNnz) return false;
   if (m.nrows > 0 && (!m.rowptr || !m.Y)) return false;
   if (m.nnz > 0 && (!m.off || !m.val || !m.X || m.ncols == 0)) return false;
   return true;

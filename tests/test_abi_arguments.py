@@ -108,6 +108,8 @@ def _cases(D):
          lambda: F("damn_spmm_dacsr16")(4, 4, 4, A16, A16, A16, 0, 0, A16, A16, N)),
         ("damn_spmm_dacsr16", bad, "bad arguments",  # entries but no column of X
          lambda: F("damn_spmm_dacsr16")(4, 0, 4, A16, A16, A16, 0, 1, A16, A16, N)),
+        ("damn_spmm_dacsr16", bad, "bad arguments",  # no headroom below INT_MAX
+         lambda: F("damn_spmm_dacsr16")(4, 4, 2**31 - 10, A16, A16, A16, 0, 1, A16, A16, N)),
         ("damn_batch_plan_create", bad, "count",
          lambda: F("damn_batch_plan_create")(-1, N, 1, 0, 0, N, out())),
         ("damn_batch_plan_create", bad, "k must be",
