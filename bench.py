@@ -160,6 +160,23 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+def max_over_ranks(t, dist, device):
+    """The slowest rank's time: N independent replicas (one per GPU) are timed
+    together, and the job takes as long as its slowest rank."""
+    if dist is None:
+        return t
+    import torch
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_value(world, units_per_step, seconds_per_step):
+    """Whole-job throughput of `world` replicas: the units every rank
+    processed in one step, over the slowest rank's step time, in 1e9 / s."""
+    return world * units_per_step / seconds_per_step / 1e9
+
+
 def _time_repeated(fn, budget_s):
     """Seconds per call of fn() repeated for about budget_s seconds (one
     untimed warm-up call first), and the number of timed calls."""
@@ -960,12 +977,7 @@ def main():
             fn(i)
         e1.record(stream)
         barrier()
-        t = e0.elapsed_time(e1) * 1e-3
-        if dist is not None:
-            tt = torch.tensor([t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        return t
+        return max_over_ranks(e0.elapsed_time(e1) * 1e-3, dist, dev)
 
     def per_step(fn, reps):
         """Each of `reps` steps bracketed by its own event pair on the
@@ -996,7 +1008,7 @@ def main():
     b_cs = spmv_bytes(n, nnz, 4, 8, 8)
     per_step_da = t_da / args.steps
     per_step_cs = t_cs / args.steps
-    value = world * b_da / per_step_da / 1e9
+    value = replica_value(world, b_da, per_step_da)
 
     # reduced-precision values (FP32 / BF16 values, FP32 vectors)
     mixed = {}
@@ -1090,14 +1102,10 @@ def main():
     run_e2e(e2e_steps)
     e1.record(stream)
     barrier()
-    t_e2e = e0.elapsed_time(e1) * 1e-3 / e2e_steps
-    if dist is not None:
-        tt = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = max_over_ranks(e0.elapsed_time(e1) * 1e-3 / e2e_steps, dist, dev)
     if not torch.equal(torch.from_numpy(hy[(e2e_steps - 1) % 2].numpy()).to(dev), dy[(e2e_steps - 1) % 2]):
         raise RuntimeError("e2e: downloaded y differs from the device result")
-    e2e_value = world * b_da / t_e2e / 1e9
+    e2e_value = replica_value(world, b_da, t_e2e)
     # the host link that bounds the end-to-end leg: one pinned copy of the
     # step's x up and of its y down, each alone (best of 5, CUDA events)
     def copy_gbs(dst, src):
