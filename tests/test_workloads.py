@@ -89,3 +89,18 @@ def test_perturb_symmetric_keeps_symmetry_and_dominance():
     assert np.all(off < d)                          # strictly diagonally dominant: SPD
     delta = (pv - val)[(pv - val) != 0]
     assert 0.008 < delta.std() < 0.012 and abs(delta.mean()) < 0.002
+
+
+def test_full_size_workloads_match_their_documented_sizes():
+    """The seeded generators give, at full size, the entry counts the
+    benchmark's byte model and the design notes quote: the 512-matrix batch
+    (12,182,394 rows, 271,862,000 entries, 2.96 GB at FP64 and k = 1) and the
+    random banded matrix n = 1e6, h = 1000 (13,551,395 entries)."""
+    mats = W.batch_banded(512)
+    assert sum(m[0] for m in mats) == 12_182_394
+    assert sum(len(m[2]) for m in mats) == 271_862_000
+    nbytes = sum((m[0] + 1) * 4 + len(m[2]) * (2 + 8) + 2 * m[0] * 8 for m in mats)
+    assert nbytes == 2_962_269_928
+    rp, c, _ = W.random_banded(1_000_000, 1000, W.rng_for(3, 0))
+    assert len(c) == 13_551_395
+    assert 13.0 < len(c) / 1e6 < 14.0
